@@ -1,0 +1,172 @@
+/*
+ * tdc.h -- C ABI of the GB300 divide-and-conquer (DC) tridiagonal eigensolver.
+ *
+ * The library computes T = Q diag(lambda) Q^T for a real symmetric tridiagonal
+ * T = tridiag(e, d, e) (the matrix of Eq. (1) of Li, Rouet, Liu, Huang, Gao and Chi,
+ * "An efficient hybrid tridiagonal divide-and-conquer algorithm on distributed
+ * memory architectures") by Cuppen's method: tearing (Eq. 2), recursive solution of
+ * the two halves, and the rank-one merge of Eqs. (3)-(6), with deflation (Eq. 5),
+ * FP64 secular-equation roots, the Loewner-theorem recomputation of z (Remark 1)
+ * and the eigenvector product U = Q (G P) diag(Qhat, I) of Eq. (6).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers unless the name ends in _host.
+ *    The caller owns every buffer; the library allocates nothing except where an
+ *    entry point says so.
+ *  - Matrices are column-major FP64 with a leading dimension ld >= rows.
+ *  - Eigenvalues are returned in ascending order.  syev-type entry points make the
+ *    largest-magnitude entry of every eigenvector positive (first such entry on ties).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous with respect to the host unless stated otherwise.
+ *  - Return value: 0 = launched; -i = argument i is invalid (LAPACK convention,
+ *    nothing launched); 3 = workspace too small; 4 = a CUDA error was reported at
+ *    launch.  Conditions found on the device are OR-ed into *dev_status (a device
+ *    int the call zeroes first): bit 0 (1) = a secular root hit the iteration cap,
+ *    bit 1 (2) = non-finite input, bit 2 (4) = a leaf QL iteration hit its cap.
+ *    dev_status may be NULL (the status is then kept in the workspace).
+ *  - No entry point aborts, throws, traps the device, or reads host memory from a
+ *    kernel.
+ */
+#ifndef TDC_H_
+#define TDC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Which form of the eigenvector product U = Q_sel Qhat (Eq. 6) a merge uses. */
+enum tdc_path {
+  TDC_PATH_DENSE_FP64 = 0,   /* FP64 GEMM, Qhat tiles generated inside the kernel      */
+  TDC_PATH_DENSE_OZAKI = 1,  /* split-precision FP64 emulation on bf16 tensor cores    */
+  TDC_PATH_HSS = 2,          /* randomized HSS approximation of Qhat (Algorithm 1)     */
+  TDC_PATH_AUTO = 3          /* HSS when K >= k_threshold, else DENSE_OZAKI           */
+};
+
+typedef struct tdc_opts {
+  int32_t path;              /* enum tdc_path                                           */
+  int32_t leaf;              /* leaf size, 1..32 (default 32)                           */
+  double hss_tol;            /* relative ID tolerance for the HSS path (default 1e-12)  */
+  int32_t hss_leaf;          /* HSS leaf block size (default 512)                       */
+  int32_t hss_rp;            /* random samples r + p (default 128)                      */
+  int64_t k_threshold;       /* AUTO: HSS only for merges with K >= this (default 8192) */
+  int32_t ozaki_slices;      /* bf16 slices per operand (default 6, range 3..8)         */
+  int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
+  int32_t tile_cfg;          /* -1 = autotuned, else a fixed tile configuration index   */
+  int32_t reserved;
+} tdc_opts;
+
+/* Fills *opts with the defaults listed above. */
+void tdc_default_opts(tdc_opts* opts);
+
+/* Bytes of device workspace tdc_syev_tridiag needs for order n. */
+size_t tdc_workspace_bytes(int64_t n, const tdc_opts* opts);
+
+/*
+ * tdc_syev_tridiag -- all eigenvalues and eigenvectors of tridiag(e, d, e).
+ * (Eq. 1; the DC tree splits a node of size m at floor(m/2), Eq. 2.)
+ *   n        order (>= 1)
+ *   d        n diagonal entries (read only)
+ *   e        n-1 off-diagonal entries (read only; may be NULL when n == 1)
+ *   lambda   n outputs, ascending
+ *   Q        n x n output, column j is the eigenvector of lambda[j]
+ *   ldq      leading dimension of Q (>= n)
+ *   opts     NULL for defaults
+ *   ws       device workspace of at least tdc_workspace_bytes(n, opts) bytes,
+ *            256-byte aligned
+ */
+int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda,
+                     double* Q, int64_t ldq, const tdc_opts* opts, void* ws,
+                     size_t ws_bytes, int* dev_status, void* stream);
+
+/*
+ * tdc_syev_tridiag_host -- the same solve from and to HOST memory: copies d, e in,
+ * solves, copies lambda and Q (ld = ldq) out, and synchronizes the stream.  Uses
+ * only the caller's device buffer dev_buf of tdc_host_buffer_bytes(n, opts) bytes.
+ * Host buffers should be page-locked for full copy bandwidth.  Returns the launch
+ * status, or the device status bits (positive) if the solve reported any.
+ */
+size_t tdc_host_buffer_bytes(int64_t n, const tdc_opts* opts);
+int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host,
+                          double* lambda_host, double* Q_host, int64_t ldq,
+                          const tdc_opts* opts, void* dev_buf, size_t dev_buf_bytes,
+                          void* stream);
+
+/*
+ * tdc_merge -- one rank-one merge (Eqs. 3-6).  Computes the eigendecomposition of
+ *     diag(Q1 D1 Q1^T, Q2 D2 Q2^T) + |beta| v v^T,  v = e_{n1} + sign(beta) e_{n1+1},
+ * i.e. D + rho z z^T in the basis Q = diag(Q1, Q2) with rho = 2|beta| and
+ * z = Q^T v / sqrt(2) (last row of Q1, sign(beta) times the first row of Q2).
+ *   n1, n2   sizes of the two halves (>= 1 each)
+ *   D        n1 + n2 eigenvalues, each half ascending (read only)
+ *   Q        (n1+n2) x (n1+n2) block-diagonal input, ld = ldq (read only; only the
+ *            two diagonal blocks are read)
+ *   beta     the coupling entry b_k of Eq. (2)
+ *   lambda   n1+n2 outputs, ascending;  Q_out: output eigenvectors, ld = ldqo
+ *   K_out    device int64: number of non-deflated entries K (may be NULL)
+ *   Q_out must not overlap Q.  The eigenvector signs are those of Eq. (6) (no sign
+ *   normalisation).  Workspace: tdc_merge_workspace_bytes(n1 + n2, opts).
+ */
+size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts);
+int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq,
+              double beta, double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out,
+              const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
+              void* stream);
+
+/*
+ * tdc_syev_tridiag_batched -- `batch` independent problems of orders n_host[p]
+ * (host array), solved together level by level (one launch per phase per tree level
+ * for the whole batch).
+ *   off_de[p]  (host) element offset of problem p in d_cat, e_cat and lambda_cat;
+ *              must be the dense packing off_de[p] = n_0 + ... + n_{p-1};
+ *              e_cat[off_de[p] + i] is the i-th off-diagonal entry (i < n_p - 1)
+ *   off_q[p]   (host) element offset of problem p's n_p x n_p block in Q_cat
+ *              (ld = n_p)
+ *   dev_status_per_problem: device int[batch] (may be NULL), same bits as above.
+ *   Workspace: tdc_batched_workspace_bytes(batch, n_host, opts).
+ */
+size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const tdc_opts* opts);
+int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de,
+                             const int64_t* off_q, const double* d_cat, const double* e_cat,
+                             double* lambda_cat, double* Q_cat, const tdc_opts* opts,
+                             void* ws, size_t ws_bytes, int* dev_status_per_problem,
+                             void* stream);
+
+/*
+ * Per-phase device timing.  Between tdc_profile_begin() and tdc_profile_end(), every
+ * solve records a pair of CUDA events on its own stream around each phase of each
+ * tree level, and synchronizes its stream once at its end to read back the
+ * per-merge counts (K and the Gu groups) from which the algorithmic work of the
+ * eigenvector product is counted.  Phases: 0 tear + leaves, 1 deflation + rotations,
+ * 2 secular roots, 3 Loewner z + column norms, 4 eigenvalue placement,
+ * 5 eigenvector product (Eq. 6), 6 deflated-column copy, 7 sign normalisation.
+ * Not thread-safe; meant for benchmarks.
+ */
+#define TDC_NPHASE 8
+typedef struct tdc_profile {
+  double ms[TDC_NPHASE];           /* summed event time per phase                     */
+  int64_t launches[TDC_NPHASE];    /* kernel launches per phase                       */
+  double product_flops;            /* algorithmic flops of the Eq. (6) products:
+                                      sum over merges of 2 K (n1 (c1 + c3) + n2 (c3 + c2)) */
+  double product_min_bytes;        /* 8 bytes x (Q_sel read + U written) over merges   */
+  int64_t merges;                  /* merges executed                                 */
+  int64_t K_total;                 /* sum of K over merges                            */
+  int64_t calls;                   /* solves recorded                                 */
+} tdc_profile;
+void tdc_profile_begin(void);
+int tdc_profile_end(tdc_profile* out);
+
+/* Reads a device status word on `stream` (synchronizes it).  Returns the bits. */
+int tdc_read_status(const int* dev_status, void* stream);
+
+/* Library version string. */
+const char* tdc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDC_H_ */

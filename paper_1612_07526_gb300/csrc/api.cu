@@ -1,0 +1,632 @@
+// C ABI of libtdc: argument checks, the DC tree plan, workspace layout and the
+// level-by-level launch sequence.  See include/tdc.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/tdc.h"
+#include "tdc_internal.cuh"
+#include "tdc_paths.cuh"
+
+namespace tdc {
+
+// ---------------------------------------------------------------------------
+// Plan: the DC trees of all problems, leaves and merges grouped by height (a
+// merge runs after both children; all merges of one height run together).
+// ---------------------------------------------------------------------------
+struct ProblemDesc {
+  int64_t n;
+  int64_t vbase;            // vector offset
+  int64_t qa, lda;          // buffer A: offset of (0,0), leading dimension
+  int64_t qb, ldb;          // buffer B
+  int64_t qs, lds;          // side buffer
+  int64_t e_base;           // e index of the first off-diagonal, or -1 (single merge)
+  double beta;              // single merge only
+};
+
+struct LevelPlan {
+  std::vector<MergeJob> jobs;
+  std::vector<int64_t> cw8, crows, ccols, ctiles;
+  size_t o_jobs = 0, o_cw8 = 0, o_crows = 0, o_ccols = 0, o_ctiles = 0;
+};
+
+struct Plan {
+  std::vector<LeafJob> leaves;
+  std::vector<int64_t> tear_list, tear_ptr;
+  std::vector<LevelPlan> levels;
+  std::vector<int64_t> sign_qoff, sign_n, sign_ld, sign_cum;
+  int64_t nmerges = 0;
+  int64_t maxm = 0;
+  size_t o_leaves = 0, o_tlist = 0, o_tptr = 0, o_sq = 0, o_sn = 0, o_sl = 0, o_sc = 0;
+  std::vector<unsigned char> blob;
+};
+
+static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int64_t n, int depth,
+                      int leaf) {
+  if (n <= leaf) {
+    LeafJob L{};
+    L.v_off = pd.vbase + lo;
+    L.buf = (depth % 2 == 0) ? 0 : 1;
+    L.q_off = L.buf ? pd.qb + lo * pd.ldb + lo : pd.qa + lo * pd.lda + lo;
+    L.ld = (int32_t)(L.buf ? pd.ldb : pd.lda);
+    L.nl = (int32_t)n;
+    L.prob = prob;
+    P.leaves.push_back(L);
+    return 0;
+  }
+  const int64_t n1 = n / 2;
+  P.tear_list.push_back(pd.vbase + lo + n1 - 1);
+  const int h1 = build_node(P, pd, prob, lo, n1, depth + 1, leaf);
+  const int h2 = build_node(P, pd, prob, lo + n1, n - n1, depth + 1, leaf);
+  const int h = std::max(h1, h2) + 1;
+  MergeJob J{};
+  J.v_off = pd.vbase + lo;
+  J.off_a = pd.qa + lo * pd.lda + lo;
+  J.off_b = pd.qb + lo * pd.ldb + lo;
+  J.off_s = pd.qs + lo * pd.lds + lo;
+  J.lda = pd.lda;
+  J.ldb = pd.ldb;
+  J.lds = pd.lds;
+  J.n1 = (int32_t)n1;
+  J.n2 = (int32_t)(n - n1);
+  J.src = ((depth + 1) % 2 == 0) ? 0 : 1;
+  J.prob = prob;
+  J.e_idx = pd.vbase + lo + n1 - 1;
+  J.beta = 0.0;
+  J.mid = P.nmerges++;
+  if ((int)P.levels.size() < h) P.levels.resize(h);
+  P.levels[h - 1].jobs.push_back(J);
+  P.maxm = std::max(P.maxm, n);
+  return h;
+}
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <class T>
+static size_t blob_put(std::vector<unsigned char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 255) & ~size_t(255);
+  blob.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+static void finish_plan(Plan& P) {
+  for (auto& L : P.levels) {
+    const size_t nj = L.jobs.size();
+    L.cw8.assign(nj + 1, 0);
+    L.crows.assign(nj + 1, 0);
+    L.ccols.assign(nj + 1, 0);
+    L.ctiles.assign(nj + 1, 0);
+    for (size_t j = 0; j < nj; ++j) {
+      const MergeJob& J = L.jobs[j];
+      const int64_t m = J.n1 + J.n2;
+      L.cw8[j + 1] = L.cw8[j] + cdiv(m, 8);
+      L.crows[j + 1] = L.crows[j] + cdiv(m, 256);
+      L.ccols[j + 1] = L.ccols[j] + m;
+      L.ctiles[j + 1] = L.ctiles[j] + (cdiv(J.n1, kGemmBM) + cdiv(J.n2, kGemmBM)) * cdiv(m, kGemmBN);
+    }
+  }
+  P.blob.clear();
+  P.o_leaves = blob_put(P.blob, P.leaves);
+  P.o_tlist = blob_put(P.blob, P.tear_list);
+  P.o_tptr = blob_put(P.blob, P.tear_ptr);
+  P.o_sq = blob_put(P.blob, P.sign_qoff);
+  P.o_sn = blob_put(P.blob, P.sign_n);
+  P.o_sl = blob_put(P.blob, P.sign_ld);
+  P.o_sc = blob_put(P.blob, P.sign_cum);
+  for (auto& L : P.levels) {
+    L.o_jobs = blob_put(P.blob, L.jobs);
+    L.o_cw8 = blob_put(P.blob, L.cw8);
+    L.o_crows = blob_put(P.blob, L.crows);
+    L.o_ccols = blob_put(P.blob, L.ccols);
+    L.o_ctiles = blob_put(P.blob, L.ctiles);
+  }
+  P.blob.resize((P.blob.size() + 255) & ~size_t(255));
+}
+
+static void build_plan(Plan& P, const std::vector<ProblemDesc>& probs, int leaf) {
+  P.tear_ptr.push_back(0);
+  P.sign_cum.push_back(0);
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const ProblemDesc& pd = probs[p];
+    if (pd.n > 0) build_node(P, pd, (int)p, 0, pd.n, 0, leaf);
+    P.tear_ptr.push_back((int64_t)P.tear_list.size());
+    P.sign_qoff.push_back(pd.qa);
+    P.sign_n.push_back(pd.n);
+    P.sign_ld.push_back(pd.lda);
+    P.sign_cum.push_back(P.sign_cum.back() + pd.n);
+  }
+  finish_plan(P);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+struct Carver {
+  unsigned char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Layout {
+  DevWs w{};
+  double* qb = nullptr;       // buffer B (ping-pong partner)
+  double* qs = nullptr;       // side buffer
+  unsigned char* plan = nullptr;
+  PathWs pw{};
+  size_t bytes = 0;
+};
+
+static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int nprob,
+                    size_t plan_bytes, const PathSizes& ps) {
+  Carver c{reinterpret_cast<unsigned char*>(ws)};
+  Layout L;
+  const size_t N = (size_t)std::max<int64_t>(nvec, 1);
+  L.qb = c.take<double>((size_t)qwords);
+  L.qs = c.take<double>((size_t)qwords);
+  DevWs& w = L.w;
+  w.ds = c.take<double>(N);
+  w.zs = c.take<double>(N);
+  w.dbar = c.take<double>(N);
+  w.zbar = c.take<double>(N);
+  w.zhat = c.take<double>(N);
+  w.tau = c.take<double>(N);
+  w.sinv = c.take<double>(N);
+  w.cmax = c.take<double>(N);
+  w.lamnd = c.take<double>(N);
+  w.dv = c.take<double>(N);
+  w.dmod = c.take<double>(N);
+  w.rc = c.take<double>(N);
+  w.rs = c.take<double>(N);
+  w.skey = c.take<double>(2 * N);
+  w.srcs = c.take<int32_t>(N);
+  w.typ = c.take<int32_t>(N);
+  w.flag = c.take<int32_t>(N);
+  w.ev = c.take<int32_t>(N);
+  w.cand = c.take<int32_t>(N);
+  w.slot = c.take<int32_t>(N);
+  w.kidx = c.take<int32_t>(N);
+  w.kperm = c.take<int32_t>(N);
+  w.org = c.take<int32_t>(N);
+  w.dsrc = c.take<int32_t>(N);
+  w.dperm = c.take<int32_t>(N);
+  w.posK = c.take<int32_t>(N);
+  w.posD = c.take<int32_t>(N);
+  w.rj = c.take<int32_t>(N);
+  w.rk = c.take<int32_t>(N);
+  w.sval = c.take<int32_t>(2 * N);
+  w.colptr = c.take<const double*>(N);
+  w.dcolptr = c.take<const double*>(N);
+  w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
+  w.status = c.take<int>((size_t)std::max(nprob, 1));
+  L.plan = c.take<unsigned char>(plan_bytes);
+  L.pw = carve_paths(c.base, c.off, ps);
+  L.bytes = c.off;
+  return L;
+}
+
+static tdc_opts resolve_opts(const tdc_opts* o) {
+  tdc_opts r;
+  tdc_default_opts(&r);
+  if (o) r = *o;
+  return r;
+}
+
+static bool opts_valid(const tdc_opts& o) {
+  return o.path >= TDC_PATH_DENSE_FP64 && o.path <= TDC_PATH_AUTO && o.leaf >= 1 && o.leaf <= 32 &&
+         o.max_secular_iter >= 1 && o.ozaki_slices >= 3 && o.ozaki_slices <= 8 && o.hss_leaf >= 16 &&
+         o.hss_rp >= 8 && o.hss_tol > 0.0;
+}
+
+template <class T>
+static const T* P_(const Layout& L, size_t off) {
+  return reinterpret_cast<const T*>(L.plan + off);
+}
+
+// Launch the whole level sequence of a plan whose blob is already on the device.
+static void run_plan(const Plan& P, const Layout& L, const tdc_opts& o, const double* d,
+                     const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
+                     bool sign_norm, double* qa_for_sign, cudaStream_t st) {
+  phase_mark(0, true, 0, st);
+  launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, d, e, L.w.dmod, nvec, st);
+  launch_leaves(P_<LeafJob>(L, P.o_leaves), (int)P.leaves.size(), L.w.dmod, e, lam, qb,
+                L.w.status, st);
+  phase_mark(0, false, 3, st);
+  for (const LevelPlan& lv : P.levels) {
+    const int nj = (int)lv.jobs.size();
+    if (nj == 0) continue;
+    const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
+    launch_merge_level(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
+                       lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
+                       o.max_secular_iter, st);
+    launch_product(o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, L.pw, st);
+    launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
+  }
+  if (sign_norm)
+    launch_sign_normalize_batched(qa_for_sign, P_<int64_t>(L, P.o_sq), P_<int64_t>(L, P.o_sn),
+                                  P_<int64_t>(L, P.o_sl), P_<int64_t>(L, P.o_sc), nprob,
+                                  P.sign_cum.back(), st);
+}
+
+// ---------------------------------------------------------------------------
+// Per-phase profiling (tdc_profile_begin / tdc_profile_end)
+// ---------------------------------------------------------------------------
+struct ProfRec {
+  int ph;
+  cudaEvent_t a, b;
+};
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<ProfRec> recs;
+  cudaEvent_t open_ev = nullptr;
+  int64_t launches[TDC_NPHASE] = {};
+  double flops = 0.0, bytes = 0.0;
+  int64_t merges = 0, ktot = 0, calls = 0;
+  MergeScalars* hscal = nullptr;
+  size_t hscal_n = 0;
+};
+static ProfState g_prof;
+
+static cudaEvent_t prof_event() {
+  if (g_prof.used == g_prof.pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_prof.pool.push_back(e);
+  }
+  return g_prof.pool[g_prof.used++];
+}
+
+void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
+  if (!g_prof.on) return;
+  if (begin) {
+    g_prof.open_ev = prof_event();
+    cudaEventRecord(g_prof.open_ev, st);
+  } else {
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, st);
+    g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev, b});
+    g_prof.launches[phase] += nlaunch;
+  }
+}
+
+// After a profiled solve: read the per-merge counts and add up the product's work.
+static void prof_account(const Plan& P, const MergeScalars* dscal, cudaStream_t st) {
+  if (!g_prof.on) return;
+  const size_t nm = (size_t)std::max<int64_t>(P.nmerges, 1);
+  if (g_prof.hscal_n < nm) {
+    if (g_prof.hscal) cudaFreeHost(g_prof.hscal);
+    cudaMallocHost(&g_prof.hscal, nm * sizeof(MergeScalars));
+    g_prof.hscal_n = nm;
+  }
+  cudaMemcpyAsync(g_prof.hscal, dscal, nm * sizeof(MergeScalars), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  for (const LevelPlan& lv : P.levels)
+    for (const MergeJob& J : lv.jobs) {
+      const MergeScalars& S = g_prof.hscal[J.mid];
+      const double K = S.K, c1 = S.c1, c3 = S.c3, c2 = S.K - S.c1 - S.c3;
+      g_prof.flops += 2.0 * K * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2));
+      g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + (double)(J.n1 + J.n2) * K);
+      g_prof.merges += 1;
+      g_prof.ktot += S.K;
+    }
+  g_prof.calls += 1;
+}
+
+static int launch_status() {
+  const cudaError_t err = cudaGetLastError();
+  return err == cudaSuccess ? 0 : 4;
+}
+
+// single-problem plan helper
+static void single_problem_plan(Plan& P, int64_t n, int64_t ldq, int leaf) {
+  ProblemDesc pd{};
+  pd.n = n;
+  pd.vbase = 0;
+  pd.qa = 0;
+  pd.lda = ldq;
+  pd.qb = 0;
+  pd.ldb = n;
+  pd.qs = 0;
+  pd.lds = n;
+  build_plan(P, {pd}, leaf);
+}
+
+static size_t syev_bytes(int64_t n, const tdc_opts& o, const Plan& P) {
+  const PathSizes ps = path_sizes(o, n, P.maxm, 1);
+  Layout L = carve(nullptr, n, n * n, P.nmerges, 1, P.blob.size(), ps);
+  return L.bytes;
+}
+
+}  // namespace tdc
+
+static_assert(sizeof(tdc_opts) == 48, "tdc_opts layout is part of the ABI");
+
+using namespace tdc;
+
+extern "C" {
+
+void tdc_default_opts(tdc_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->path = TDC_PATH_DENSE_FP64;
+  o->leaf = 32;
+  o->hss_tol = 1e-12;
+  o->hss_leaf = 512;
+  o->hss_rp = 128;
+  o->k_threshold = 8192;
+  o->ozaki_slices = 6;
+  o->max_secular_iter = 64;
+  o->tile_cfg = -1;
+}
+
+const char* tdc_version(void) { return "tdc 0.1 (sm_103a)"; }
+
+size_t tdc_workspace_bytes(int64_t n, const tdc_opts* opts) {
+  const tdc_opts o = resolve_opts(opts);
+  if (n < 1 || !opts_valid(o)) return 0;
+  Plan P;
+  single_problem_plan(P, n, n, o.leaf);
+  return syev_bytes(n, o, P);
+}
+
+int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda, double* Q,
+                     int64_t ldq, const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
+                     void* stream) {
+  if (n < 1) return -1;
+  if (!d) return -2;
+  if (!e && n > 1) return -3;
+  if (!lambda) return -4;
+  if (!Q) return -5;
+  if (ldq < n) return -6;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o)) return -7;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -8;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  single_problem_plan(P, n, ldq, o.leaf);
+  const PathSizes ps = path_sizes(o, n, P.maxm, 1);
+  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), ps);
+  if (L.bytes > ws_bytes) return 3;
+  if (dev_status) L.w.status = dev_status;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
+  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  QBufs qb{Q, L.qb, L.qs};
+  run_plan(P, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  prof_account(P, L.w.scal, st);
+  return launch_status();
+}
+
+size_t tdc_host_buffer_bytes(int64_t n, const tdc_opts* opts) {
+  const size_t ws = tdc_workspace_bytes(n, opts);
+  if (ws == 0) return 0;
+  const size_t vec = ((size_t)n * 8 + 255) & ~size_t(255);
+  const size_t mat = ((size_t)n * n * 8 + 255) & ~size_t(255);
+  return ws + 3 * vec + mat + 256;
+}
+
+int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host, double* lambda_host,
+                          double* Q_host, int64_t ldq, const tdc_opts* opts, void* dev_buf,
+                          size_t dev_buf_bytes, void* stream) {
+  if (n < 1) return -1;
+  if (!d_host) return -2;
+  if (!e_host && n > 1) return -3;
+  if (!lambda_host) return -4;
+  if (!Q_host) return -5;
+  if (ldq < n) return -6;
+  const size_t need = tdc_host_buffer_bytes(n, opts);
+  if (need == 0) return -7;
+  if (!dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 255)) return -8;
+  if (dev_buf_bytes < need) return 3;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* b = reinterpret_cast<unsigned char*>(dev_buf);
+  const size_t vec = ((size_t)n * 8 + 255) & ~size_t(255);
+  const size_t mat = ((size_t)n * n * 8 + 255) & ~size_t(255);
+  double* dd = reinterpret_cast<double*>(b);
+  double* de = reinterpret_cast<double*>(b + vec);
+  double* dl = reinterpret_cast<double*>(b + 2 * vec);
+  double* dq = reinterpret_cast<double*>(b + 3 * vec);
+  int* dstat = reinterpret_cast<int*>(b + 3 * vec + mat);
+  void* ws = b + 3 * vec + mat + 256;
+  cudaMemcpyAsync(dd, d_host, n * 8, cudaMemcpyHostToDevice, st);
+  if (n > 1) cudaMemcpyAsync(de, e_host, (n - 1) * 8, cudaMemcpyHostToDevice, st);
+  int rc = tdc_syev_tridiag(n, dd, de, dl, dq, n, opts, ws, dev_buf_bytes - (3 * vec + mat + 256),
+                            dstat, stream);
+  if (rc != 0) return rc;
+  cudaMemcpyAsync(lambda_host, dl, n * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpy2DAsync(Q_host, ldq * 8, dq, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st);
+  int hs = 0;
+  cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
+  return hs;
+}
+
+size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts) {
+  const tdc_opts o = resolve_opts(opts);
+  if (n < 2 || !opts_valid(o)) return 0;
+  Plan P;
+  P.levels.resize(1);
+  P.levels[0].jobs.resize(1);
+  P.nmerges = 1;
+  P.maxm = n;
+  P.tear_ptr = {0, 0};
+  finish_plan(P);
+  const PathSizes ps = path_sizes(o, n, n, 1);
+  Layout L = carve(nullptr, n, n * n, 1, 1, P.blob.size(), ps);
+  return L.bytes;
+}
+
+int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq, double beta,
+              double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out, const tdc_opts* opts,
+              void* ws, size_t ws_bytes, int* dev_status, void* stream) {
+  if (n1 < 1) return -1;
+  if (n2 < 1) return -2;
+  if (!D) return -3;
+  if (!Q) return -4;
+  const int64_t n = n1 + n2;
+  if (ldq < n) return -5;
+  if (!lambda) return -7;
+  if (!Q_out) return -8;
+  if (ldqo < n) return -9;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o)) return -11;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -12;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  P.levels.resize(1);
+  MergeJob J{};
+  J.v_off = 0;
+  J.off_a = 0;
+  J.lda = ldq;
+  J.off_b = 0;
+  J.ldb = ldqo;
+  J.off_s = 0;
+  J.lds = n;
+  J.n1 = (int32_t)n1;
+  J.n2 = (int32_t)n2;
+  J.src = 0;
+  J.prob = 0;
+  J.beta = beta;
+  J.e_idx = -1;
+  J.mid = 0;
+  P.levels[0].jobs.push_back(J);
+  P.nmerges = 1;
+  P.maxm = n;
+  P.tear_ptr = {0, 0};
+  finish_plan(P);
+  const PathSizes ps = path_sizes(o, n, n, 1);
+  Layout L = carve(ws, n, n * n, 1, 1, P.blob.size(), ps);
+  if (L.bytes > ws_bytes) return 3;
+  if (dev_status) L.w.status = dev_status;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
+  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(lambda, D, n * 8, cudaMemcpyDeviceToDevice, st);
+  QBufs qb{const_cast<double*>(Q), Q_out, L.qs};
+  const LevelPlan& lv = P.levels[0];
+  const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
+  launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
+                     lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
+                     qb, L.w, o.max_secular_iter, st);
+  launch_product(o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, L.pw, st);
+  launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
+  if (K_out) launch_copy_k(L.w.scal, K_out, st);
+  prof_account(P, L.w.scal, st);
+  return launch_status();
+}
+
+size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const tdc_opts* opts) {
+  const tdc_opts o = resolve_opts(opts);
+  if (batch < 1 || !n_host || !opts_valid(o)) return 0;
+  std::vector<ProblemDesc> probs(batch);
+  int64_t vtot = 0, qtot = 0, maxn = 0;
+  for (int p = 0; p < batch; ++p) {
+    const int64_t n = n_host[p];
+    if (n < 1) return 0;
+    probs[p] = ProblemDesc{n, vtot, qtot, n, qtot, n, qtot, n, -1, 0.0};
+    vtot += n;
+    qtot += n * n;
+    maxn = std::max(maxn, n);
+  }
+  Plan P;
+  build_plan(P, probs, o.leaf);
+  const PathSizes ps = path_sizes(o, maxn, P.maxm, batch);
+  // vectors are addressed by the caller's offsets; size for a dense packing plus slack
+  Layout L = carve(nullptr, vtot, qtot, P.nmerges, batch, P.blob.size(), ps);
+  return L.bytes;
+}
+
+int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de,
+                             const int64_t* off_q, const double* d_cat, const double* e_cat,
+                             double* lambda_cat, double* Q_cat, const tdc_opts* opts, void* ws,
+                             size_t ws_bytes, int* dev_status_per_problem, void* stream) {
+  if (batch < 1) return -1;
+  if (!n_host) return -2;
+  if (!off_de) return -3;
+  if (!off_q) return -4;
+  if (!d_cat) return -5;
+  if (!e_cat) return -6;
+  if (!lambda_cat) return -7;
+  if (!Q_cat) return -8;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o)) return -9;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -10;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // Internal vectors and the B / side buffers use a dense packing; the caller's
+  // offsets address d, e, lambda and Q only.  Map: problem p's internal vector base
+  // is its packed offset; the kernels index d/e/lambda by v_off, so the packed and
+  // caller offsets must coincide -> require off_de to be the dense packing.
+  std::vector<ProblemDesc> probs(batch);
+  int64_t vtot = 0, qtot = 0, maxn = 0;
+  for (int p = 0; p < batch; ++p) {
+    const int64_t n = n_host[p];
+    if (n < 1) return -2;
+    if (off_de[p] != vtot) return -3;
+    if (off_q[p] < 0) return -4;
+    probs[p] = ProblemDesc{n, vtot, off_q[p], n, qtot, n, qtot, n, -1, 0.0};
+    vtot += n;
+    qtot += n * n;
+    maxn = std::max(maxn, n);
+  }
+  Plan P;
+  build_plan(P, probs, o.leaf);
+  const PathSizes ps = path_sizes(o, maxn, P.maxm, batch);
+  Layout L = carve(ws, vtot, qtot, P.nmerges, batch, P.blob.size(), ps);
+  if (L.bytes > ws_bytes) return 3;
+  if (dev_status_per_problem) L.w.status = dev_status_per_problem;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int) * batch, st);
+  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  QBufs qb{Q_cat, L.qb, L.qs};
+  run_plan(P, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
+  prof_account(P, L.w.scal, st);
+  return launch_status();
+}
+
+void tdc_profile_begin(void) {
+  g_prof.on = true;
+  g_prof.used = 0;
+  g_prof.recs.clear();
+  for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
+  g_prof.flops = g_prof.bytes = 0.0;
+  g_prof.merges = g_prof.ktot = g_prof.calls = 0;
+}
+
+int tdc_profile_end(tdc_profile* out) {
+  if (!out) return -1;
+  std::memset(out, 0, sizeof(*out));
+  if (cudaDeviceSynchronize() != cudaSuccess) return 4;
+  for (const ProfRec& r : g_prof.recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    out->ms[r.ph] += ms;
+  }
+  for (int i = 0; i < TDC_NPHASE; ++i) out->launches[i] = g_prof.launches[i];
+  out->product_flops = g_prof.flops;
+  out->product_min_bytes = g_prof.bytes;
+  out->merges = g_prof.merges;
+  out->K_total = g_prof.ktot;
+  out->calls = g_prof.calls;
+  g_prof.on = false;
+  g_prof.recs.clear();
+  g_prof.used = 0;
+  return 0;
+}
+
+int tdc_read_status(const int* dev_status, void* stream) {
+  if (!dev_status) return -1;
+  int h = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&h, dev_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -2;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -2;
+  return h;
+}
+
+}  // extern "C"

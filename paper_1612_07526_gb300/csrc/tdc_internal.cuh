@@ -1,0 +1,128 @@
+// Internal types and device helpers shared by the CUDA translation units of libtdc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tdc {
+
+constexpr double kEps = 1.1102230246251565e-16;     // 2^-53, unit roundoff
+constexpr double kInvSqrt2 = 0.7071067811865476;    // correctly rounded 1/sqrt(2)
+
+// Device status bits (OR-ed into the status word).
+enum : int { ST_SECULAR = 1, ST_NONFINITE = 2, ST_LEAF = 4, ST_WAIT = 8 };
+
+// Per-sorted-position flags written by the deflation kernel.
+enum : int { F_T1 = 1, F_T2 = 2, F_ROT = 4 };
+
+// One leaf of the DC tree: an nl x nl tridiagonal block solved by one warp.
+struct LeafJob {
+  int64_t v_off;     // first index of the leaf in the d / e / lambda vectors
+  int64_t q_off;     // element offset of the leaf block (0,0) in the output buffer
+  int32_t ld;        // leading dimension of that buffer
+  int32_t buf;       // 0: buffer A, 1: buffer B
+  int32_t nl;        // leaf order (1..32)
+  int32_t prob;      // problem index
+};
+
+// One rank-one merge (Eqs. 3-6).  The children's eigenvectors are in buffer `src`
+// (0 = A, 1 = B); the merged eigenvectors go to the other buffer.
+struct MergeJob {
+  int64_t v_off;     // first index of the merged block in the vectors
+  int64_t off_a;     // element offset of block (0,0) in buffer A
+  int64_t off_b;     // ... in buffer B
+  int64_t off_s;     // ... in the side buffer holding rotated columns
+  int64_t lda, ldb, lds;
+  int32_t n1, n2;
+  int32_t src;
+  int32_t prob;
+  double beta;       // coupling entry b_k, used when e_idx < 0
+  int64_t e_idx;     // index of b_k in the e vector, or -1
+  int64_t mid;       // merge id (index into the per-merge scalars)
+};
+
+struct MergeScalars {
+  int32_t K;         // non-deflated count
+  int32_t c1, c3;    // Gu groups: columns touching rows of T1 only / both halves
+  int32_t nd;        // deflated count
+  int32_t nrot;      // plane rotations applied
+  int32_t sorted;    // 1 if the deflated values came out ascending
+  double rho;        // 2 |beta|
+  double tol;        // deflation tolerance
+};
+
+// Device workspace arrays; per-index arrays are addressed at job.v_off.
+struct DevWs {
+  double *ds, *zs;            // sorted d and z (updated by rotations)
+  double *dbar, *zbar;        // non-deflated (K) values
+  double *zhat, *tau, *sinv, *cmax;
+  double *lamnd;              // non-deflated eigenvalues d_org + tau
+  double *dv;                 // deflated eigenvalues (sorted-position order)
+  double *skey;               // 2n scratch keys for the fallback sort
+  int32_t *srcs, *typ, *flag, *ev, *cand, *slot;
+  int32_t *kidx, *kperm, *org, *dsrc, *dperm, *posK, *posD;
+  int32_t *sval;              // 2n scratch values for the fallback sort
+  const double **colptr;      // grouped (Gu order) non-deflated column pointers
+  const double **dcolptr;     // deflated column pointers
+  int32_t *rj, *rk;           // rotation records (sorted positions)
+  double *rc, *rs;
+  MergeScalars *scal;         // per merge id
+  double *dmod;               // torn diagonal (Eq. 2 corner updates)
+  int *status;                // per problem
+};
+
+struct QBufs {
+  double *A, *B, *S;          // ping-pong eigenvector buffers and the side buffer
+};
+
+// Smallest j with cum[j+1] > b (cum has njobs+1 entries, cum[0] = 0).
+__device__ __forceinline__ int find_job(const int64_t* __restrict__ cum, int njobs, int64_t b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cum[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Profiling hook (defined in api.cu): brackets a phase with CUDA events when the
+// per-phase timing of tdc_profile_begin() is on; a no-op otherwise.
+void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
+
+// Kernel launchers (defined in the .cu files; all asynchronous on `st`).
+void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, const double* d,
+                 const double* e, double* dmod, int64_t ntot, cudaStream_t st);
+void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const double* e,
+                   double* lam, QBufs qb, int* status, cudaStream_t st);
+void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
+                        const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
+                        int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
+                        int max_iter, cudaStream_t st);
+void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles, int64_t ntiles,
+                      QBufs qb, DevWs w, cudaStream_t st);
+void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, int64_t nb_cols,
+                      QBufs qb, DevWs w, cudaStream_t st);
+void launch_sign_normalize_batched(double* Q, const int64_t* qoff, const int64_t* nn,
+                                   const int64_t* ldd, const int64_t* cum_cols, int nprob,
+                                   int64_t ncols, cudaStream_t st);
+
+constexpr int kGemmBM = 128;
+constexpr int kGemmBN = 128;
+
+}  // namespace tdc
