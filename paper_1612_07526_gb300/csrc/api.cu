@@ -161,12 +161,13 @@ struct Layout {
   double* qb = nullptr;       // buffer B (ping-pong partner)
   double* qs = nullptr;       // side buffer
   unsigned char* plan = nullptr;
-  PathWs pw{};
+  unsigned char* arena = nullptr;
+  unsigned char* table = nullptr;
   size_t bytes = 0;
 };
 
 static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int nprob,
-                    size_t plan_bytes, const PathSizes& ps) {
+                    size_t plan_bytes, const PathPlan& ps) {
   Carver c{reinterpret_cast<unsigned char*>(ws)};
   Layout L;
   const size_t N = (size_t)std::max<int64_t>(nvec, 1);
@@ -208,7 +209,8 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
   w.status = c.take<int>((size_t)std::max(nprob, 1));
   L.plan = c.take<unsigned char>(plan_bytes);
-  L.pw = carve_paths(c.base, c.off, ps);
+  L.table = c.take<unsigned char>(ps.table_bytes);
+  L.arena = c.take<unsigned char>(ps.arena_bytes);
   L.bytes = c.off;
   return L;
 }
@@ -232,22 +234,30 @@ static const T* P_(const Layout& L, size_t off) {
 }
 
 // Launch the whole level sequence of a plan whose blob is already on the device.
-static void run_plan(const Plan& P, const Layout& L, const tdc_opts& o, const double* d,
-                     const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
+static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
+  std::vector<const std::vector<MergeJob>*> v;
+  for (const LevelPlan& lv : P.levels) v.push_back(&lv.jobs);
+  return v;
+}
+
+static void run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const tdc_opts& o,
+                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
                      bool sign_norm, double* qa_for_sign, cudaStream_t st) {
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, d, e, L.w.dmod, nvec, st);
   launch_leaves(P_<LeafJob>(L, P.o_leaves), (int)P.leaves.size(), L.w.dmod, e, lam, qb,
                 L.w.status, st);
   phase_mark(0, false, 3, st);
-  for (const LevelPlan& lv : P.levels) {
+  for (size_t li = 0; li < P.levels.size(); ++li) {
+    const LevelPlan& lv = P.levels[li];
     const int nj = (int)lv.jobs.size();
     if (nj == 0) continue;
     const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
     launch_merge_level(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                        lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
                        o.max_secular_iter, st);
-    launch_product(o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, L.pw, st);
+    launch_product(pp, (int)li, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w,
+                   st);
     launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
   }
   if (sign_norm)
@@ -342,8 +352,9 @@ static void single_problem_plan(Plan& P, int64_t n, int64_t ldq, int leaf) {
 }
 
 static size_t syev_bytes(int64_t n, const tdc_opts& o, const Plan& P) {
-  const PathSizes ps = path_sizes(o, n, P.maxm, 1);
-  Layout L = carve(nullptr, n, n * n, P.nmerges, 1, P.blob.size(), ps);
+  PathPlan pp;
+  path_prepare(pp, o, level_jobs(P));
+  Layout L = carve(nullptr, n, n * n, P.nmerges, 1, P.blob.size(), pp);
   return L.bytes;
 }
 
@@ -394,14 +405,17 @@ int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Plan P;
   single_problem_plan(P, n, ldq, o.leaf);
-  const PathSizes ps = path_sizes(o, n, P.maxm, 1);
-  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), ps);
+  PathPlan pp;
+  const auto lj = level_jobs(P);
+  path_prepare(pp, o, lj);
+  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp);
   if (L.bytes > ws_bytes) return 3;
   if (dev_status) L.w.status = dev_status;
   cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   QBufs qb{Q, L.qb, L.qs};
-  run_plan(P, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
   prof_account(P, L.w.scal, st);
   return launch_status();
 }
@@ -459,9 +473,12 @@ size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts) {
   P.nmerges = 1;
   P.maxm = n;
   P.tear_ptr = {0, 0};
+  P.levels[0].jobs[0].n1 = (int32_t)(n / 2);
+  P.levels[0].jobs[0].n2 = (int32_t)(n - n / 2);
   finish_plan(P);
-  const PathSizes ps = path_sizes(o, n, n, 1);
-  Layout L = carve(nullptr, n, n * n, 1, 1, P.blob.size(), ps);
+  PathPlan pp;
+  path_prepare(pp, o, level_jobs(P));
+  Layout L = carve(nullptr, n, n * n, 1, 1, P.blob.size(), pp);
   return L.bytes;
 }
 
@@ -503,12 +520,15 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   P.maxm = n;
   P.tear_ptr = {0, 0};
   finish_plan(P);
-  const PathSizes ps = path_sizes(o, n, n, 1);
-  Layout L = carve(ws, n, n * n, 1, 1, P.blob.size(), ps);
+  PathPlan pp;
+  const auto lj = level_jobs(P);
+  path_prepare(pp, o, lj);
+  Layout L = carve(ws, n, n * n, 1, 1, P.blob.size(), pp);
   if (L.bytes > ws_bytes) return 3;
   if (dev_status) L.w.status = dev_status;
   cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   cudaMemcpyAsync(lambda, D, n * 8, cudaMemcpyDeviceToDevice, st);
   QBufs qb{const_cast<double*>(Q), Q_out, L.qs};
   const LevelPlan& lv = P.levels[0];
@@ -516,7 +536,7 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
                      qb, L.w, o.max_secular_iter, st);
-  launch_product(o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, L.pw, st);
+  launch_product(pp, 0, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, st);
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
   prof_account(P, L.w.scal, st);
@@ -538,9 +558,9 @@ size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const t
   }
   Plan P;
   build_plan(P, probs, o.leaf);
-  const PathSizes ps = path_sizes(o, maxn, P.maxm, batch);
-  // vectors are addressed by the caller's offsets; size for a dense packing plus slack
-  Layout L = carve(nullptr, vtot, qtot, P.nmerges, batch, P.blob.size(), ps);
+  PathPlan pp;
+  path_prepare(pp, o, level_jobs(P));
+  Layout L = carve(nullptr, vtot, qtot, P.nmerges, batch, P.blob.size(), pp);
   return L.bytes;
 }
 
@@ -578,14 +598,17 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
   }
   Plan P;
   build_plan(P, probs, o.leaf);
-  const PathSizes ps = path_sizes(o, maxn, P.maxm, batch);
-  Layout L = carve(ws, vtot, qtot, P.nmerges, batch, P.blob.size(), ps);
+  PathPlan pp;
+  const auto lj = level_jobs(P);
+  path_prepare(pp, o, lj);
+  Layout L = carve(ws, vtot, qtot, P.nmerges, batch, P.blob.size(), pp);
   if (L.bytes > ws_bytes) return 3;
   if (dev_status_per_problem) L.w.status = dev_status_per_problem;
   cudaMemsetAsync(L.w.status, 0, sizeof(int) * batch, st);
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   QBufs qb{Q_cat, L.qb, L.qs};
-  run_plan(P, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
+  run_plan(P, pp, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
   prof_account(P, L.w.scal, st);
   return launch_status();
 }

@@ -1,0 +1,622 @@
+// Split-precision eigenvector product of Eq. (6) on tcgen05 tensor cores.
+// See tdc_ozaki.cuh for the splitting and the exactness argument.
+//
+// Kernels (one launch each per tree level, over that level's merges):
+//   k_oz_slice_a  rows of Q_sel (gathered columns, Gu order, padded groups): row
+//                 scale, then S bf16 digit slices written k-major;
+//   k_oz_slice_b  Qhat generated from (d, zhat, origin, tau, 1/norm) and split the
+//                 same way, one column of Qhat per k-major row;
+//   k_oz_gemm     128 x 64 output tiles: a TMA producer warp, an MMA warp and four
+//                 epilogue warps.  Seven to eight FP32 accumulators of 64 TMEM
+//                 columns (one per level p + q); exact levels are flushed every
+//                 256 k into 64-bit integers held by the epilogue threads.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "tdc_ozaki.cuh"
+
+namespace tdc {
+
+namespace {
+
+constexpr int kThreads = 192;       // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr long long kWaitNs = 10LL * 1000 * 1000 * 1000;   // bounded mbarrier waits (10 s)
+
+__host__ __device__ constexpr int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// padded k (Gu groups each padded to kOzPad) -> grouped index in [0, K), or -1
+__device__ __forceinline__ int padded_to_grouped(int k, int c1, int c3, int K, int P1, int P3) {
+  if (k < P1) return k < c1 ? k : -1;
+  if (k < P1 + P3) return (k - P1) < c3 ? c1 + (k - P1) : -1;
+  const int r = k - P1 - P3;
+  return r < K - c1 - c3 ? c1 + c3 + r : -1;
+}
+
+// Balanced base-256 digits of X (|X| <= 2^(8S-1)), most significant first, as bf16 bits.
+template <int S>
+__device__ __forceinline__ void digits_bf16(long long X, uint16_t (&out)[S]) {
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    const long long d = ((X + 128) & 255) - 128;
+    out[p] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+    X = (X - d) >> 8;
+  }
+  out[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)X));
+}
+
+// ------------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity; gives up after kWaitNs or when another
+// role has aborted, setting the abort flag and the status bit.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicOr(err, ST_WAIT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(dst), "l"(map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups
+// 512 bytes apart (SM100 descriptor: start >> 4, LBO, SBO >> 4, version 1, layout 4).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
+                            ((uint32_t)(kOzBM >> 4) << 24);
+
+struct JobView {
+  int jb;
+  int64_t local;
+};
+__device__ __forceinline__ JobView job_of(const int64_t* cum, int njobs) {
+  JobView v;
+  v.jb = find_job(cum, njobs, blockIdx.x);
+  v.local = blockIdx.x - cum[v.jb];
+  return v;
+}
+
+// ------------------------------------------------------------------------ slicing of Q_sel
+template <int S>
+__global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__ jobs,
+                                                    const OzJob* __restrict__ ozj, int njobs,
+                                                    const int64_t* __restrict__ cum, DevWs w) {
+  __shared__ double tile[64][33];
+  __shared__ double s_max[8][32];
+  __shared__ int s_exp[32];
+  const JobView jv = job_of(cum, njobs);
+  const MergeJob J = jobs[jv.jb];
+  const OzJob& Z = ozj[jv.jb];
+  const MergeScalars Sc = w.scal[J.mid];
+  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
+  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
+  const int nrt1 = (J.n1 + 31) / 32;
+  const int h = jv.local < nrt1 ? 0 : 1;
+  const int rt = h ? (int)jv.local - nrt1 : (int)jv.local;
+  const int rows_h = h ? J.n2 : J.n1;
+  const int rowbase = h ? J.n1 : 0;
+  const int r0 = rt * 32;
+  const int kb = h ? P1 : 0;
+  const int klen = h ? P3 + P2 : P1 + P3;
+  const double* const* colptr = w.colptr + J.v_off;
+  const int tid = threadIdx.x;
+  const int r = tid & 31, kq = tid >> 5;
+  const bool rvalid = r0 + r < rows_h;
+  // pass 1: row maxima
+  double mx = 0.0;
+  for (int k = kq; k < klen; k += 8) {
+    const int kg = padded_to_grouped(kb + k, c1, c3, K, P1, P3);
+    if (kg >= 0 && rvalid) mx = fmax(mx, fabs(colptr[kg][rowbase + r0 + r]));
+  }
+  s_max[kq][r] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    double m = s_max[0][tid];
+    for (int q = 1; q < 8; ++q) m = fmax(m, s_max[q][tid]);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);     // m < 2^e
+    s_exp[tid] = e;
+    if (r0 + tid < rows_h) Z.sigma[rowbase + r0 + tid] = m > 0.0 ? ldexp(1.0, e) : 0.0;
+  }
+  __syncthreads();
+  // pass 2: digits, 64 k at a time, transposed through shared memory
+  const int wr = tid >> 3, wk = (tid & 7) * 8;
+  const int shift = 8 * S - 1 - s_exp[wr];
+  uint16_t* abase = Z.a[h];
+  for (int k0 = 0; k0 < klen; k0 += 64) {
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = kq * 8 + kk;
+      const int kg = padded_to_grouped(kb + k0 + k, c1, c3, K, P1, P3);
+      tile[k][r] = (kg >= 0 && rvalid && k0 + k < klen) ? colptr[kg][rowbase + r0 + r] : 0.0;
+    }
+    __syncthreads();
+    if (r0 + wr < rows_h) {
+      uint16_t dg[8][S];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const double x = tile[wk + j][wr];
+        const long long X = __double2ll_rn(ldexp(x, shift));
+        uint16_t t[S];
+        digits_bf16<S>(X, t);
+#pragma unroll
+        for (int p = 0; p < S; ++p) dg[j][p] = t[p];
+      }
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
+        uint4 v;
+        v.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+        v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+        v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+        v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+        *reinterpret_cast<uint4*>(abase + ((int64_t)p * rows_h + r0 + wr) * Z.ldk + k0 + wk) = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------ generated, sliced Qhat
+template <int S>
+__global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__ jobs,
+                                                    const OzJob* __restrict__ ozj, int njobs,
+                                                    const int64_t* __restrict__ cum, DevWs w) {
+  const JobView jv = job_of(cum, njobs);
+  const MergeJob J = jobs[jv.jb];
+  const OzJob& Z = ozj[jv.jb];
+  const int m = J.n1 + J.n2;
+  const int64_t nkc = (Z.ldk + 2047) / 2048;
+  const int i = (int)(jv.local / nkc);
+  const int kc = (int)(jv.local % nkc);
+  const MergeScalars Sc = w.scal[J.mid];
+  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
+  if (i >= K || i >= m) return;
+  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
+  const int KP = P1 + P3 + P2;
+  const int64_t o = J.v_off;
+  const double* __restrict__ dbar = w.dbar + o;
+  const double* __restrict__ zhat = w.zhat + o;
+  const int32_t* __restrict__ kperm = w.kperm + o;
+  const double dorg = dbar[w.org[o + i]];
+  const double t = w.tau[o + i];
+  const double si = w.sinv[o + i];
+  int e = 0;
+  const double cm = w.cmax[o + i];
+  if (cm > 0.0) frexp(cm, &e);
+  if (kc == 0 && threadIdx.x == 0) Z.texp[i] = e;
+  const int shift = 8 * S - 1 - e;
+  const int k0 = kc * 2048 + threadIdx.x * 8;
+  if (k0 >= Z.ldk) return;
+  uint16_t dg[8][S];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = k0 + j;
+    const int kg = k < KP ? padded_to_grouped(k, c1, c3, K, P1, P3) : -1;
+    double v = 0.0;
+    if (kg >= 0) {
+      const int jj = kperm[kg];
+      v = (zhat[jj] / ((dbar[jj] - dorg) - t)) * si;
+    }
+    uint16_t tt[S];
+    digits_bf16<S>(__double2ll_rn(ldexp(v, shift)), tt);
+#pragma unroll
+    for (int p = 0; p < S; ++p) dg[j][p] = tt[p];
+  }
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+    uint4 vv;
+    vv.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+    vv.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+    vv.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+    vv.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+    *reinterpret_cast<uint4*>(Z.b + ((int64_t)p * m + i) * Z.ldk + k0) = vv;
+  }
+}
+
+// ------------------------------------------------------------------------ tcgen05 GEMM
+template <int S>
+struct OzCfg {
+  static constexpr int NL = S + 1;                       // levels 2 .. S+2
+  static constexpr int ST = S <= 6 ? 3 : 2;              // pipeline stages
+  static constexpr int A_BYTES = kOzBM * kOzBK * 2 * S;
+  static constexpr int B_BYTES = kOzBN * kOzBK * 2 * S;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = ST * STAGE + 1024 + 256;
+  static_assert(NL * kOzBN <= 512, "TMEM columns");
+};
+
+template <int S>
+__global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restrict__ jobs,
+                                                         const OzJob* __restrict__ ozj, int njobs,
+                                                         const int64_t* __restrict__ cum, QBufs qb,
+                                                         DevWs w) {
+  using C = OzCfg<S>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::ST * C::STAGE);
+  // bars[0..ST) full, [ST..2ST) empty, 2ST accfull, 2ST+1 accempty, 2ST+2 done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::ST + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const JobView jv = job_of(cum, njobs);
+  const MergeJob J = jobs[jv.jb];
+  const OzJob* Z = ozj + jv.jb;
+  int* err = w.status + J.prob;
+  const MergeScalars Sc = w.scal[J.mid];
+  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
+  const int m = J.n1 + J.n2;
+  const int nct = (m + kOzBN - 1) / kOzBN;
+  const int nrt1 = (J.n1 + kOzBM - 1) / kOzBM;
+  const int ct = (int)(jv.local % nct);
+  const int rtl = (int)(jv.local / nct);
+  if (ct * kOzBN >= K) return;                            // uniform: no barrier touched yet
+  const int h = rtl < nrt1 ? 0 : 1;
+  const int row0 = (h ? rtl - nrt1 : rtl) * kOzBM;        // within the half
+  const int rows_h = h ? J.n2 : J.n1;
+  const int rowbase = h ? J.n1 : 0;
+  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
+  const int klen = h ? P3 + P2 : P1 + P3;
+  const int kb = h ? P1 : 0;
+  const int nst = klen / kOzBK;
+  const int nchunks = (nst + kOzChunk / kOzBK - 1) / (kOzChunk / kOzBK);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (C::ST + s); };
+  const uint32_t accfull = bar0 + 8u * (2 * C::ST);
+  const uint32_t accempty = bar0 + 8u * (2 * C::ST + 1);
+  const uint32_t done = bar0 + 8u * (2 * C::ST + 2);
+
+  if (tid == 0) {
+    for (int s = 0; s < C::ST; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, 4);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && nst > 0) {
+      // ---------------- TMA producer
+      const CUtensorMap* mA = &Z->mapA[h];
+      const CUtensorMap* mB = &Z->mapB;
+      asm volatile("prefetch.tensormap [%0];" ::"l"(mA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(mB) : "memory");
+      int issued = 0;
+      for (int it = 0; it < nst; ++it) {
+        const int s = it % C::ST;
+        const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, err)) break;
+        const uint32_t sa = smem_u32(smem + s * C::STAGE);
+        mbar_expect_tx(full(s), C::STAGE);
+        tma_load_3d(sa, mA, full(s), it * kOzBK, row0, 0);
+        tma_load_3d(sa + C::A_BYTES, mB, full(s), kb + it * kOzBK, ct * kOzBN, 0);
+        issued = it + 1;
+      }
+      if (*abort_flag) {      // let the copies in flight land before the CTA exits
+        const long long t0 = global_ns();
+        for (int it = (issued > C::ST ? issued - C::ST : 0); it < issued; ++it) {
+          const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
+          while (!mbar_try(full(it % C::ST), ph) && global_ns() - t0 < kWaitNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nst > 0) {
+      // ---------------- MMA issuer
+      const int per_chunk = kOzChunk / kOzBK;
+      uint32_t started = 0;                 // tail accumulators already written
+      for (int it = 0; it < nst; ++it) {
+        const int s = it % C::ST;
+        const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
+        if (!mbar_wait(full(s), ph, abort_flag, err)) break;
+        tc_fence_after();
+        const int chunk = it / per_chunk;
+        const bool first = (it % per_chunk) == 0;
+        const bool last = (it % per_chunk) == per_chunk - 1 || it == nst - 1;
+        const uint32_t sa = smem_u32(smem + s * C::STAGE);
+        const uint32_t sb = sa + C::A_BYTES;
+        bool ok = true;
+#pragma unroll
+        for (int kk = 0; kk < kOzBK / 16; ++kk) {
+          // tail levels 6 .. S+2 (never reset after their first write)
+#pragma unroll
+          for (int L = 6; L <= S + 2; ++L) {
+#pragma unroll
+            for (int p = (L - S > 1 ? L - S : 1); p <= (S < L - 1 ? S : L - 1); ++p) {
+              const int q = L - p;
+              const uint32_t bit = 1u << L;
+              const uint32_t acc = (started & bit) ? 1u : 0u;
+              started |= bit;
+              tc_mma(tmem + (uint32_t)((L - 2) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                     sdesc(sb + (q - 1) * (kOzBN * kOzBK * 2) + kk * 32), kIdesc, acc);
+            }
+          }
+          if (first && kk == 0 && chunk > 0) {
+            if (!mbar_wait(accempty, (uint32_t)(chunk - 1) & 1u, abort_flag, err)) { ok = false; break; }
+            tc_fence_after();
+          }
+          // exact levels 2 .. 5, restarted at every chunk
+#pragma unroll
+          for (int L = 2; L <= 5; ++L) {
+#pragma unroll
+            for (int p = 1; p <= L - 1; ++p) {
+              const int q = L - p;
+              const uint32_t acc = (first && kk == 0 && p == 1) ? 0u : 1u;
+              tc_mma(tmem + (uint32_t)((L - 2) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                     sdesc(sb + (q - 1) * (kOzBN * kOzBK * 2) + kk * 32), kIdesc, acc);
+            }
+          }
+        }
+        if (!ok) break;
+        tc_commit(empty(s));
+        if (last) tc_commit(accfull);
+      }
+      tc_commit(done);
+      if (*abort_flag) mbar_wait(done, 0, abort_flag, err);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+    long long acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      if (!mbar_wait(accfull, (uint32_t)c & 1u, abort_flag, err)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int L = 2; L <= 5; ++L) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            acc[hh * 32 + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty);
+    }
+    if (ok && nst > 0) {
+      ok = mbar_wait(done, 0, abort_flag, err);
+      tc_fence_after();
+    }
+    const int grow = row0 + row;
+    if (ok && grow < rows_h) {
+      const double sig = Z->sigma[rowbase + grow];
+      double* out = J.src ? qb.A + J.off_a : qb.B + J.off_b;
+      const int64_t ld = J.src ? J.lda : J.ldb;
+      const int32_t* posK = w.posK + J.v_off;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        double dv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dv[j] = ldexp((double)acc[hh * 32 + j], -38);
+        if (nst > 0) {
+#pragma unroll
+          for (int L = 6; L <= S + 2; ++L) {
+            uint32_t v[32];
+            tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dv[j] += ldexp((double)__uint_as_float(v[j]), -(14 + 8 * (L - 2)));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = ct * kOzBN + hh * 32 + j;
+          if (col < K) out[(int64_t)posK[col] * ld + rowbase + grow] = ldexp(dv[j] * sig, Z->texp[col]);
+        }
+      }
+    } else if (nst > 0 && grow < rows_h) {
+      // keep the tcgen05.ld pattern uniform across the warp even when this row is idle
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int L = 6; L <= S + 2; ++L) {
+          if (!ok) break;
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
+          tmem_wait_ld();
+        }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+template <int S>
+void launch_s(const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa, int64_t nb_sa,
+              const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t, int64_t ntiles, QBufs qb,
+              DevWs w, int* err, cudaStream_t st) {
+  using C = OzCfg<S>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    attr = true;
+  }
+  if (nb_sa) k_oz_slice_a<S><<<(unsigned)nb_sa, 256, 0, st>>>(jobs, ozj, njobs, cum_sa, w);
+  if (nb_sb) k_oz_slice_b<S><<<(unsigned)nb_sb, 256, 0, st>>>(jobs, ozj, njobs, cum_sb, w);
+  (void)err;
+  if (ntiles) k_oz_gemm<S><<<(unsigned)ntiles, kThreads, C::SMEM, st>>>(jobs, ozj, njobs, cum_t, qb, w);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode3d(CUtensorMap* map, void* base, int64_t ldk, int64_t rows, int slices, int box_rows) {
+  auto fn = encoder();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)slices};
+  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(ldk * rows * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)slices};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t job_ldk(const MergeJob& J) { return rup((int64_t)J.n1 + J.n2 + 3 * kOzPad, kOzPad); }
+
+}  // namespace
+
+size_t oz_job_bytes(const MergeJob& J, int slices) {
+  const int64_t m = J.n1 + J.n2, ldk = job_ldk(J);
+  size_t b = 0;
+  b += rup(slices * (int64_t)J.n1 * ldk * 2, 256);
+  b += rup(slices * (int64_t)J.n2 * ldk * 2, 256);
+  b += rup(slices * m * ldk * 2, 256);
+  b += rup(m * 8, 256);
+  b += rup(m * 4, 256);
+  return b;
+}
+
+bool oz_fill_job(OzJob& z, const MergeJob& J, unsigned char* base, int slices) {
+  std::memset(&z, 0, sizeof(z));
+  const int64_t m = J.n1 + J.n2, ldk = job_ldk(J);
+  size_t off = 0;
+  z.a[0] = reinterpret_cast<uint16_t*>(base + off);
+  off += rup(slices * (int64_t)J.n1 * ldk * 2, 256);
+  z.a[1] = reinterpret_cast<uint16_t*>(base + off);
+  off += rup(slices * (int64_t)J.n2 * ldk * 2, 256);
+  z.b = reinterpret_cast<uint16_t*>(base + off);
+  off += rup(slices * m * ldk * 2, 256);
+  z.sigma = reinterpret_cast<double*>(base + off);
+  off += rup(m * 8, 256);
+  z.texp = reinterpret_cast<int32_t*>(base + off);
+  z.ldk = ldk;
+  z.slices = slices;
+  bool ok = encode3d(&z.mapA[0], z.a[0], ldk, J.n1, slices, kOzBM);
+  ok = ok && encode3d(&z.mapA[1], z.a[1], ldk, J.n2, slices, kOzBM);
+  ok = ok && encode3d(&z.mapB, z.b, ldk, m, slices, kOzBN);
+  return ok;
+}
+
+int64_t oz_blocks_slice_a(const MergeJob& J) { return (J.n1 + 31) / 32 + (J.n2 + 31) / 32; }
+int64_t oz_blocks_slice_b(const MergeJob& J) {
+  return (int64_t)(J.n1 + J.n2) * ((job_ldk(J) + 2047) / 2048);
+}
+int64_t oz_tiles(const MergeJob& J) {
+  const int64_t m = J.n1 + J.n2;
+  return ((J.n1 + kOzBM - 1) / kOzBM + (J.n2 + kOzBM - 1) / kOzBM) * ((m + kOzBN - 1) / kOzBN);
+}
+
+void launch_ozaki_level(const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
+                        int64_t nb_sa, const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t,
+                        int64_t ntiles, int slices, QBufs qb, DevWs w, int* err, cudaStream_t st) {
+  switch (slices) {
+    case 5: launch_s<5>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
+    case 7: launch_s<7>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
+    default: launch_s<6>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
+  }
+}
+
+}  // namespace tdc

@@ -1,39 +1,101 @@
 // Product-path dispatch (see tdc_paths.cuh).
+#include <cstring>
+
+#include "tdc_ozaki.cuh"
 #include "tdc_paths.cuh"
 
 namespace tdc {
 
 namespace {
 __global__ void k_copy_k(const MergeScalars* scal, int64_t* k_out) { *k_out = scal[0].K; }
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
-PathSizes path_sizes(const tdc_opts& o, int64_t maxn, int64_t maxm, int nprob) {
-  (void)o;
-  (void)maxn;
-  (void)maxm;
-  (void)nprob;
-  return PathSizes{};
+bool path_supported(const tdc_opts& o) {
+  return o.path == TDC_PATH_DENSE_FP64 || o.path == TDC_PATH_DENSE_OZAKI;
 }
 
-PathWs carve_paths(unsigned char* base, size_t& off, const PathSizes& ps) {
-  off = (off + 255) & ~size_t(255);
-  PathWs pw;
-  pw.base = base ? base + off : nullptr;
-  pw.bytes = ps.bytes;
-  off += ps.bytes;
-  return pw;
+void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv) {
+  pp.levels.assign(lv.size(), PathLevel{});
+  pp.slices = o.ozaki_slices < 5 ? 5 : (o.ozaki_slices > 7 ? 7 : o.ozaki_slices);
+  pp.arena_bytes = 0;
+  size_t tab = 0;
+  if (o.path != TDC_PATH_DENSE_OZAKI) {
+    pp.table_bytes = 0;
+    return;
+  }
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const auto& jobs = *lv[l];
+    int64_t maxm = 0;
+    for (const MergeJob& J : jobs) maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
+    PathLevel& L = pp.levels[l];
+    if (jobs.empty() || maxm < kOzMinOrder) continue;
+    L.oz = true;
+    size_t arena = 0;
+    for (const MergeJob& J : jobs) arena += al(oz_job_bytes(J, pp.slices));
+    pp.arena_bytes = std::max(pp.arena_bytes, arena);
+    L.tab_off = tab;
+    tab = al(tab + jobs.size() * sizeof(OzJob));
+    for (int c = 0; c < 3; ++c) {
+      L.cum_off[c] = tab;
+      tab = al(tab + (jobs.size() + 1) * sizeof(int64_t));
+    }
+  }
+  pp.table_bytes = tab;
 }
 
-bool path_supported(const tdc_opts& o) { return o.path == TDC_PATH_DENSE_FP64; }
+bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
+               const std::vector<const std::vector<MergeJob>*>& lv, cudaStream_t st) {
+  pp.arena_dev = arena;
+  pp.table_dev = table_dev;
+  if (pp.table_bytes == 0) return true;
+  pp.table_store.assign(pp.table_bytes / 8 + 64, 0);
+  pp.table = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(pp.table_store.data()) + 255) & ~uintptr_t(255));
+  bool ok = true;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    PathLevel& L = pp.levels[l];
+    if (!L.oz) continue;
+    const auto& jobs = *lv[l];
+    OzJob* z = reinterpret_cast<OzJob*>(pp.table + L.tab_off);
+    int64_t* cum[3];
+    for (int c = 0; c < 3; ++c) {
+      cum[c] = reinterpret_cast<int64_t*>(pp.table + L.cum_off[c]);
+      cum[c][0] = 0;
+    }
+    size_t off = 0;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+      ok = ok && oz_fill_job(z[j], jobs[j], arena + off, pp.slices);
+      off += al(oz_job_bytes(jobs[j], pp.slices));
+      cum[0][j + 1] = cum[0][j] + oz_blocks_slice_a(jobs[j]);
+      cum[1][j + 1] = cum[1][j] + oz_blocks_slice_b(jobs[j]);
+      cum[2][j + 1] = cum[2][j] + oz_tiles(jobs[j]);
+    }
+    for (int c = 0; c < 3; ++c) L.nb[c] = cum[c][jobs.size()];
+  }
+  cudaMemcpyAsync(table_dev, pp.table, pp.table_bytes, cudaMemcpyHostToDevice, st);
+  return ok;
+}
 
-void launch_product(const tdc_opts& o, const std::vector<MergeJob>& hjobs, const MergeJob* jobs,
-                    const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w, PathWs pw,
+void launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
+                    const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
                     cudaStream_t st) {
   (void)o;
-  (void)pw;
   phase_mark(5, true, 0, st);
-  launch_gemm_fp64(jobs, (int)hjobs.size(), cum_tiles, ntiles, qb, w, st);
-  phase_mark(5, false, 1, st);
+  const PathLevel* L = (l >= 0 && l < (int)pp.levels.size()) ? &pp.levels[l] : nullptr;
+  if (L && L->oz) {
+    const OzJob* z = reinterpret_cast<const OzJob*>(pp.table_dev + L->tab_off);
+    const int64_t* c0 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[0]);
+    const int64_t* c1 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[1]);
+    const int64_t* c2 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[2]);
+    launch_ozaki_level(jobs, z, (int)hjobs.size(), c0, L->nb[0], c1, L->nb[1], c2, L->nb[2], pp.slices, qb,
+                       w, nullptr, st);
+    phase_mark(5, false, 3, st);
+  } else {
+    launch_gemm_fp64(jobs, (int)hjobs.size(), cum_tiles, ntiles, qb, w, st);
+    phase_mark(5, false, 1, st);
+  }
 }
 
 void launch_copy_k(const MergeScalars* scal, int64_t* k_out, cudaStream_t st) {

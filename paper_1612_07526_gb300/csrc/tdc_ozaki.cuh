@@ -1,0 +1,60 @@
+// Split-precision (Ozaki-style) FP64 emulation of the eigenvector product of Eq. (6)
+// on the bf16 tensor cores (tcgen05.mma kind::f16 with FP32 accumulation in TMEM).
+//
+// Splitting.  Every row r of Q_sel (restricted to the k-range its half uses) is
+// scaled by a power of two sigma_r >= max_k |Q_sel[r, k]| and every column i of Qhat
+// by tau_i >= max_k |Qhat[k, i]|.  The scaled values x in [-1, 1] are rounded to
+// X = rint(x 2^(8S-1)) and written in balanced base 256:
+//     x ~= sum_{p=1..S} 2^(-7-8(p-1)) a_p,   a_1 in [-128, 128], a_p in [-128, 127],
+// each digit exact in bf16; the representation error is at most 2^(-8S) per entry.
+// Then  (Q_sel Qhat)[r, i] = sigma_r tau_i sum_{p,q} 2^(-14-8(p+q-2)) (a_p . b_q)[r, i]
+// and the sum is kept for levels L = p + q <= S + 2.
+//
+// Exactness.  |a_p b_q| <= 2^14, so a level-L sum of at most 4 pairs over 256 k is
+// an integer of magnitude <= 2^24: levels 2..5 are accumulated in FP32 (exactly)
+// over chunks of 256 k and each chunk is flushed into a 64-bit integer accumulator
+// (LSB = the level-5 unit).  Levels 6..S+2 carry weights below 2^-46 relative and
+// are accumulated in FP32 over the whole k range.
+#pragma once
+
+#include <cuda.h>
+
+#include <vector>
+
+#include "tdc_internal.cuh"
+
+namespace tdc {
+
+constexpr int kOzBM = 128;          // tile rows (one TMEM lane per row)
+constexpr int kOzBN = 64;           // tile columns (one TMEM column block per level)
+constexpr int kOzBK = 32;           // k per pipeline stage (64-byte swizzled rows)
+constexpr int kOzChunk = 256;       // k per exact chunk
+constexpr int kOzPad = 64;          // padding of the Gu groups in the k coordinate
+
+struct OzJob {                      // CUtensorMap members force 64+ byte alignment
+  CUtensorMap mapA[2];              // A slices of the T1 rows (0) and T2 rows (1)
+  CUtensorMap mapB;                 // B slices (columns of Qhat)
+  uint16_t* a[2];                   // a[h] + ((p * rows_h) + r) * ldk + k
+  uint16_t* b;                      // b + ((q * m) + i) * ldk + k
+  double* sigma;                    // per merge-local row: power-of-two row scale
+  int32_t* texp;                    // per column: tau_i = 2^texp
+  int64_t ldk;                      // padded k extent
+  int32_t slices;
+  int32_t pad_;
+};
+
+// Host side: bytes of the per-merge slice arena, and filling an OzJob for a merge
+// whose arena starts at `base` (256-byte aligned).
+size_t oz_job_bytes(const MergeJob& J, int slices);
+bool oz_fill_job(OzJob& z, const MergeJob& J, unsigned char* base, int slices);
+
+// Launches the slicing kernels and the tcgen05 GEMM for one level's merges.
+void launch_ozaki_level(const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
+                        int64_t nb_sa, const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t,
+                        int64_t ntiles, int slices, QBufs qb, DevWs w, int* err, cudaStream_t st);
+// Units per job for the three launches (host).
+int64_t oz_blocks_slice_a(const MergeJob& J);
+int64_t oz_blocks_slice_b(const MergeJob& J);
+int64_t oz_tiles(const MergeJob& J);
+
+}  // namespace tdc

@@ -1,4 +1,5 @@
-// Dispatch of the eigenvector product of Eq. (6) to its implementations, and the
+// Dispatch of the eigenvector product of Eq. (6) to its implementations (native
+// FP64 with in-kernel Qhat tiles, or the split-precision tcgen05 path), and the
 // workspace each implementation needs.
 #pragma once
 
@@ -9,24 +10,36 @@
 
 namespace tdc {
 
-struct PathSizes {
-  size_t bytes = 0;          // extra workspace bytes of the chosen product path
+struct PathLevel {
+  bool oz = false;
+  size_t tab_off = 0;        // OzJob array of the level in the table region
+  size_t cum_off[3] = {0, 0, 0};
+  int64_t nb[3] = {0, 0, 0}; // blocks: slice A, slice B, GEMM tiles
 };
 
-struct PathWs {
-  unsigned char* base = nullptr;
-  size_t bytes = 0;
+struct PathPlan {
+  std::vector<PathLevel> levels;
+  size_t arena_bytes = 0;    // slice arena (reused level after level)
+  size_t table_bytes = 0;    // OzJob arrays + launch tables
+  std::vector<uint64_t> table_store;   // host image of the table region (aligned below)
+  unsigned char* table = nullptr;
+  unsigned char* arena_dev = nullptr;
+  unsigned char* table_dev = nullptr;
+  int slices = 6;
 };
 
-// Workspace of the product path for problems of order <= maxn whose largest merge
-// has order maxm (nprob problems).
-PathSizes path_sizes(const tdc_opts& o, int64_t maxn, int64_t maxm, int nprob);
-// Carves the path workspace at base + *off (advancing *off); base may be null.
-PathWs carve_paths(unsigned char* base, size_t& off, const PathSizes& ps);
+// Merges of order below this use the FP64 product even on the split path.
+constexpr int64_t kOzMinOrder = 1024;
+
 bool path_supported(const tdc_opts& o);
-// Launches the product for all merges of one level (host copy of the jobs in hjobs).
-void launch_product(const tdc_opts& o, const std::vector<MergeJob>& hjobs, const MergeJob* jobs,
-                    const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w, PathWs pw,
+// Decides the product form per level and sizes its workspace (no device access).
+void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv);
+// Binds the carved device regions, encodes the tensor maps and uploads the tables.
+bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
+               const std::vector<const std::vector<MergeJob>*>& lv, cudaStream_t st);
+// Launches the product for all merges of level l.
+void launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
+                    const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
                     cudaStream_t st);
 void launch_copy_k(const MergeScalars* scal, int64_t* k_out, cudaStream_t st);
 
