@@ -53,6 +53,7 @@ static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int6
     L.ld = (int32_t)(L.buf ? pd.ldb : pd.lda);
     L.nl = (int32_t)n;
     L.prob = prob;
+    L.root = depth == 0 ? 1 : 0;
     P.leaves.push_back(L);
     return 0;
   }
@@ -76,6 +77,7 @@ static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int6
   J.e_idx = pd.vbase + lo + n1 - 1;
   J.beta = 0.0;
   J.mid = P.nmerges++;
+  J.root = depth == 0 ? 1 : 0;
   if ((int)P.levels.size() < h) P.levels.resize(h);
   P.levels[h - 1].jobs.push_back(J);
   P.maxm = std::max(P.maxm, n);
@@ -244,7 +246,8 @@ static void run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const t
                      const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
                      bool sign_norm, double* qa_for_sign, cudaStream_t st) {
   phase_mark(0, true, 0, st);
-  launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, d, e, L.w.dmod, nvec, st);
+  launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
+              o.leaf, d, e, L.w.dmod, nvec, st);
   launch_leaves(P_<LeafJob>(L, P.o_leaves), (int)P.leaves.size(), L.w.dmod, e, lam, qb,
                 L.w.status, st);
   phase_mark(0, false, 3, st);
@@ -258,12 +261,11 @@ static void run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const t
                        o.max_secular_iter, st);
     launch_product(pp, (int)li, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w,
                    st);
-    launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
+    bool any_root = false;
+    for (const MergeJob& J : lv.jobs) any_root |= J.root != 0;
+    launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, sign_norm && any_root, st);
   }
-  if (sign_norm)
-    launch_sign_normalize_batched(qa_for_sign, P_<int64_t>(L, P.o_sq), P_<int64_t>(L, P.o_sn),
-                                  P_<int64_t>(L, P.o_sl), P_<int64_t>(L, P.o_sc), nprob,
-                                  P.sign_cum.back(), st);
+  (void)qa_for_sign;
 }
 
 // ---------------------------------------------------------------------------
@@ -537,7 +539,7 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
                      qb, L.w, o.max_secular_iter, st);
   launch_product(pp, 0, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, st);
-  launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, st);
+  launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
   prof_account(P, L.w.scal, st);
   return launch_status();

@@ -18,17 +18,24 @@ namespace {
 
 constexpr int BM = kGemmBM, BN = kGemmBN, BK = 8, NT = 256;
 
-__global__ __launch_bounds__(NT) void k_gemm_fp64(const MergeJob* __restrict__ jobs, int njobs,
-                                                  const int64_t* __restrict__ cum, QBufs qb,
-                                                  DevWs w) {
-  __shared__ double As[2][BK][BM];
-  __shared__ double Bs[2][BK][BN];
-  __shared__ double s_dorg[BN], s_tau[BN], s_sinv[BN];
-  __shared__ int s_pos[BN];
+struct GemmSmem {
+  double As[2][BK][BM];
+  double Bs[2][BK][BN];
+  double dorg[BN], tau[BN], sinv[BN];
+  int pos[BN];
+};
 
-  const int jb = find_job(cum, njobs, blockIdx.x);
+__device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJob* __restrict__ jobs,
+                                          int njobs, const int64_t* __restrict__ cum, QBufs qb, DevWs w) {
+  auto& As = sm.As;
+  auto& Bs = sm.Bs;
+  double* s_dorg = sm.dorg;
+  double* s_tau = sm.tau;
+  double* s_sinv = sm.sinv;
+  int* s_pos = sm.pos;
+  const int jb = find_job(cum, njobs, vb);
   const MergeJob J = jobs[jb];
-  const int64_t tile = blockIdx.x - cum[jb];
+  const int64_t tile = vb - cum[jb];
   const int n1 = J.n1, n2 = J.n2, m = n1 + n2;
   const int nrt1 = (n1 + BM - 1) / BM, nrt2 = (n2 + BM - 1) / BM;
   const int ct = (int)(tile / (nrt1 + nrt2));
@@ -156,12 +163,23 @@ __global__ __launch_bounds__(NT) void k_gemm_fp64(const MergeJob* __restrict__ j
   }
 }
 
+// Grid-stride over the level's tiles: tiles of columns beyond K cost a few loads.
+__global__ __launch_bounds__(NT) void k_gemm_fp64(int64_t ntiles, const MergeJob* __restrict__ jobs,
+                                                  int njobs, const int64_t* __restrict__ cum, QBufs qb,
+                                                  DevWs w) {
+  __shared__ GemmSmem sm;
+  for (int64_t vb = blockIdx.x; vb < ntiles; vb += gridDim.x) {
+    gemm_tile(vb, sm, jobs, njobs, cum, qb, w);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles, int64_t ntiles,
                       QBufs qb, DevWs w, cudaStream_t st) {
   if (ntiles == 0) return;
-  k_gemm_fp64<<<(unsigned)ntiles, NT, 0, st>>>(jobs, njobs, cum_tiles, qb, w);
+  k_gemm_fp64<<<grid_cap(ntiles, 1), NT, 0, st>>>(ntiles, jobs, njobs, cum_tiles, qb, w);
 }
 
 }  // namespace tdc

@@ -444,7 +444,9 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       if (*abort_flag) mbar_wait(done, 0, abort_flag, err);
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4.
+    // Every tcgen05.ld below is executed by all 32 lanes (.sync.aligned); only the
+    // global stores are predicated on the row being inside the half.
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
@@ -452,8 +454,9 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      if (!mbar_wait(accfull, (uint32_t)c & 1u, abort_flag, err)) { ok = false; break; }
+    for (int c = 0; c < nchunks; ++c) {
+      const bool got = __all_sync(0xffffffffu, mbar_wait(accfull, (uint32_t)c & 1u, abort_flag, err));
+      if (!got) { ok = false; break; }
       tc_fence_after();
 #pragma unroll
       for (int L = 2; L <= 5; ++L) {
@@ -472,12 +475,13 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       if (lane == 0) mbar_arrive(accempty);
     }
     if (ok && nst > 0) {
-      ok = mbar_wait(done, 0, abort_flag, err);
+      ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag, err));
       tc_fence_after();
     }
     const int grow = row0 + row;
-    if (ok && grow < rows_h) {
-      const double sig = Z->sigma[rowbase + grow];
+    const bool rv = grow < rows_h;
+    if (ok) {
+      const double sig = rv ? Z->sigma[rowbase + grow] : 0.0;
       double* out = J.src ? qb.A + J.off_a : qb.B + J.off_b;
       const int64_t ld = J.src ? J.lda : J.ldb;
       const int32_t* posK = w.posK + J.v_off;
@@ -496,23 +500,14 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
             for (int j = 0; j < 32; ++j) dv[j] += ldexp((double)__uint_as_float(v[j]), -(14 + 8 * (L - 2)));
           }
         }
+        if (rv) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = ct * kOzBN + hh * 32 + j;
-          if (col < K) out[(int64_t)posK[col] * ld + rowbase + grow] = ldexp(dv[j] * sig, Z->texp[col]);
+          for (int j = 0; j < 32; ++j) {
+            const int col = ct * kOzBN + hh * 32 + j;
+            if (col < K) out[(int64_t)posK[col] * ld + rowbase + grow] = ldexp(dv[j] * sig, Z->texp[col]);
+          }
         }
       }
-    } else if (nst > 0 && grow < rows_h) {
-      // keep the tcgen05.ld pattern uniform across the warp even when this row is idle
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-        for (int L = 6; L <= S + 2; ++L) {
-          if (!ok) break;
-          uint32_t v[32];
-          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
-          tmem_wait_ld();
-        }
     }
   }
   tc_fence_before();

@@ -23,6 +23,8 @@ struct LeafJob {
   int32_t buf;       // 0: buffer A, 1: buffer B
   int32_t nl;        // leaf order (1..32)
   int32_t prob;      // problem index
+  int32_t root;      // 1 if the leaf is the whole problem (sign convention applied)
+  int32_t pad_;
 };
 
 // One rank-one merge (Eqs. 3-6).  The children's eigenvectors are in buffer `src`
@@ -39,6 +41,8 @@ struct MergeJob {
   double beta;       // coupling entry b_k, used when e_idx < 0
   int64_t e_idx;     // index of b_k in the e vector, or -1
   int64_t mid;       // merge id (index into the per-merge scalars)
+  int32_t root;      // 1 for the top merge of a problem whose output gets the sign convention
+  int32_t pad_;
 };
 
 struct MergeScalars {
@@ -105,9 +109,12 @@ __device__ __forceinline__ double warp_prod(double v) {
 // per-phase timing of tdc_profile_begin() is on; a no-op otherwise.
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
 
+// Grid size for a grid-stride kernel: min(nb, SMs x per_sm), at least 1.
+unsigned grid_cap(int64_t nb, int per_sm);
+
 // Kernel launchers (defined in the .cu files; all asynchronous on `st`).
-void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, const double* d,
-                 const double* e, double* dmod, int64_t ntot, cudaStream_t st);
+void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, int64_t ntear, int leaf,
+                 const double* d, const double* e, double* dmod, int64_t ntot, cudaStream_t st);
 void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const double* e,
                    double* lam, QBufs qb, int* status, cudaStream_t st);
 void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
@@ -117,7 +124,7 @@ void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, 
 void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles, int64_t ntiles,
                       QBufs qb, DevWs w, cudaStream_t st);
 void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, int64_t nb_cols,
-                      QBufs qb, DevWs w, cudaStream_t st);
+                      QBufs qb, DevWs w, bool any_root, cudaStream_t st);
 void launch_sign_normalize_batched(double* Q, const int64_t* qoff, const int64_t* nn,
                                    const int64_t* ldd, const int64_t* cum_cols, int nprob,
                                    int64_t ncols, cudaStream_t st);
