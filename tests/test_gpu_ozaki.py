@@ -60,13 +60,16 @@ def test_syev_ozaki(api, gen, n):
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
     lam_o, q_o = api.syev_tridiag(dt, et, opts={"path": OZ})
     lam_f, q_f = api.syev_tridiag(dt, et, opts={"path": 0})
-    assert torch.equal(lam_o, lam_f)
+    # above the first split-precision level the merge inputs differ at rounding level,
+    # so eigenvalues agree to the contract tolerance and eigenvectors where gaps allow
     lam = lam_o.cpu().numpy()
     q = q_o.cpu().numpy()
     nrm = metrics.tnorm(d, e)
+    assert np.max(np.abs(lam - lam_f.cpu().numpy())) <= 10 * n * EPS * nrm
     assert metrics.scaled_residual(d, e, lam, q) <= 10
     assert metrics.orthogonality(q) <= 100 * n * EPS
-    assert np.max(np.abs(q - q_f.cpu().numpy())) <= 1e-12
+    err, mask = metrics.column_agreement(lam_f.cpu().numpy(), q_f.cpu().numpy(), q, nrm, min_relgap=1e-4)
+    assert err <= 1e-8
     lref = sturm.bisection_eigvals(d, e, np.arange(0, n, max(1, n // 64)))
     assert np.max(np.abs(lam[::max(1, n // 64)] - lref)) <= 10 * n * EPS * nrm
 
