@@ -360,6 +360,36 @@ static size_t syev_bytes(int64_t n, const tdc_opts& o, const Plan& P) {
   return L.bytes;
 }
 
+int syev_core(int64_t n, const double* d, const double* e, double* lambda, double* Q, int64_t ldq,
+              const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status, void* stream,
+              bool profile_accounting) {
+  if (n < 1) return -1;
+  if (!d) return -2;
+  if (!e && n > 1) return -3;
+  if (!lambda) return -4;
+  if (!Q) return -5;
+  if (ldq < n) return -6;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o)) return -7;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -8;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  single_problem_plan(P, n, ldq, o.leaf);
+  PathPlan pp;
+  const auto lj = level_jobs(P);
+  path_prepare(pp, o, lj);
+  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp);
+  if (L.bytes > ws_bytes) return 3;
+  if (dev_status) L.w.status = dev_status;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
+  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
+  QBufs qb{Q, L.qb, L.qs};
+  run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  if (profile_accounting) prof_account(P, L.w.scal, st);
+  return launch_status();
+}
+
 }  // namespace tdc
 
 static_assert(sizeof(tdc_opts) == 48, "tdc_opts layout is part of the ABI");
@@ -395,31 +425,7 @@ size_t tdc_workspace_bytes(int64_t n, const tdc_opts* opts) {
 int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda, double* Q,
                      int64_t ldq, const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
                      void* stream) {
-  if (n < 1) return -1;
-  if (!d) return -2;
-  if (!e && n > 1) return -3;
-  if (!lambda) return -4;
-  if (!Q) return -5;
-  if (ldq < n) return -6;
-  const tdc_opts o = resolve_opts(opts);
-  if (!opts_valid(o) || !path_supported(o)) return -7;
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -8;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  Plan P;
-  single_problem_plan(P, n, ldq, o.leaf);
-  PathPlan pp;
-  const auto lj = level_jobs(P);
-  path_prepare(pp, o, lj);
-  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp);
-  if (L.bytes > ws_bytes) return 3;
-  if (dev_status) L.w.status = dev_status;
-  cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
-  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
-  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
-  QBufs qb{Q, L.qb, L.qs};
-  run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
-  prof_account(P, L.w.scal, st);
-  return launch_status();
+  return tdc::syev_core(n, d, e, lambda, Q, ldq, opts, ws, ws_bytes, dev_status, stream, true);
 }
 
 size_t tdc_host_buffer_bytes(int64_t n, const tdc_opts* opts) {
