@@ -159,6 +159,29 @@ typedef struct tdc_profile {
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);
 
+/*
+ * tdc_syev_tridiag_noalloc -- tdc_syev_tridiag with default options for orders
+ * n <= TDC_NOALLOC_MAX_N, for callers that cannot allocate device memory: code
+ * running under an allocator that forbids new device allocations, plug-ins handed
+ * only the input and output buffers by their host application, or paths where an
+ * allocation would synchronize the device.  The paper has no counterpart; this is an
+ * interface convenience.
+ *   The workspace is a fixed array of TDC_NOALLOC_SCRATCH_BYTES inside the library,
+ *   held on every GPU that loads it until the process exits.  The caller passes
+ *   inputs and outputs only (device pointers, as for tdc_syev_tridiag).  The first
+ *   call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   Calls share the array: calls whose work overlaps on the GPU (different streams,
+ *   or the same array used from two host threads without ordering) race.  The call
+ *   clears what must start at zero (the status word when dev_status is NULL) and
+ *   calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Returns -1 if n < 1 or n > TDC_NOALLOC_MAX_N, otherwise as tdc_syev_tridiag.
+ */
+#define TDC_NOALLOC_MAX_N 512
+#define TDC_NOALLOC_SCRATCH_BYTES (6u << 20)
+int tdc_syev_tridiag_noalloc(int64_t n, const double* d, const double* e, double* lambda,
+                             double* Q, int64_t ldq, int* dev_status, void* stream);
+
 /* Reads a device status word on `stream` (synchronizes it).  Returns the bits. */
 int tdc_read_status(const int* dev_status, void* stream);
 

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("tdc_syev_tridiag_batched", ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _OPT, _P,
                                                 ctypes.c_size_t, _P, _P]),
     ("tdc_read_status", ctypes.c_int, [_P, _P]),
+    ("tdc_syev_tridiag_noalloc", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
     ("tdc_profile_begin", None, []),
     ("tdc_profile_end", ctypes.c_int, [ctypes.POINTER(TdcProfile)]),
     ("tdc_version", ctypes.c_char_p, []),
