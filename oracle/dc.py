@@ -301,6 +301,39 @@ def merge(D: np.ndarray, Q: np.ndarray, n1: int, beta: float):
     return lam_all[fin], vec_all[:, fin], info
 
 
+def merge_hss(D: np.ndarray, Q: np.ndarray, n1: int, beta: float, leaf: int, rp: int, tol: float,
+              seed: int):
+    """The merge of ``merge`` with Qhat replaced by its HSS approximation (Section 2.2):
+    Qhat, in the order of the sorted non-deflated d, is compressed by Algorithm 1 with
+    the Gaussian sampling matrices Omega1 = G(seed, 1), Omega2 = G(seed, 2)
+    (``hss.gaussian_matrix``), and Q_sel Qhat is formed by the HSS multiply."""
+    from . import hss
+    lam, u, info = merge(D, Q, n1, beta)
+    kk = info["K"]
+    if kk == 0:
+        return lam, u, info
+    n = D.shape[0]
+    order = info["order"]
+    cols = np.asarray(Q, dtype=np.float64)[:, order].copy()
+    for (j, k, c, s) in info["rotations"]:
+        cj, ck = cols[:, j].copy(), cols[:, k].copy()
+        cols[:, j] = c * cj + s * ck
+        cols[:, k] = -s * cj + c * ck
+    qsel = cols[:, info["kept"]]
+    om1 = hss.gaussian_matrix(seed, 1, kk, rp)
+    om2 = hss.gaussian_matrix(seed, 2, kk, rp)
+    root, nodes = hss.rand_hss(info["qhat"], om1, om2, leaf, tol)
+    u_nd = hss.hss_left_multiply(qsel, root, nodes)
+    # place the non-deflated columns where ``merge`` put them
+    fin = info["final_order"]
+    out = u.copy()
+    pos = np.empty(n, dtype=np.int64)
+    pos[fin] = np.arange(n)
+    out[:, pos[:kk]] = u_nd
+    info = dict(info, hss_ranks=hss.hss_ranks(nodes))
+    return lam, out, info
+
+
 # ----------------------------------------------------------------------------
 # The DC tree (PDSTEDC analogue).
 # ----------------------------------------------------------------------------

@@ -23,6 +23,36 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(seed: int, idx) -> np.ndarray:
+    """Output number idx (0-based) of the SplitMix64 sequence seeded with `seed`
+    (Steele, Lea and Flood, 2014): z = seed + (idx+1) * gamma, then the two
+    xor-shift-multiply rounds and a final xor-shift, all modulo 2^64."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (idx + np.uint64(1)) * np.uint64(SPLITMIX_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def gaussian_matrix(seed: int, stream: int, rows: int, cols: int) -> np.ndarray:
+    """rows x cols standard normal matrix (column-major element order) by Box-Muller:
+    element (r, c) with q = stream * 2^40 + c * rows + r uses draws 2q and 2q+1,
+    u1 = (draw >> 11 + 1) 2^-53 in (0, 1], u2 = (draw >> 11) 2^-53, and
+    g = sqrt(-2 ln u1) cos(2 pi u2).  These are the random sampling matrices of
+    Algorithm 1 as the library draws them."""
+    r = np.arange(rows, dtype=np.uint64)[:, None]
+    c = np.arange(cols, dtype=np.uint64)[None, :]
+    q = np.uint64(stream) * np.uint64(1 << 40) + c * np.uint64(rows) + r
+    z1 = splitmix64(seed, np.uint64(2) * q)
+    z2 = splitmix64(seed, np.uint64(2) * q + np.uint64(1))
+    u1 = ((z1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = (z2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
 
 class Node:
     __slots__ = ("idx", "lo", "hi", "left", "right", "parent", "level",

@@ -105,7 +105,7 @@ static void finish_plan(Plan& P) {
       const MergeJob& J = L.jobs[j];
       const int64_t m = J.n1 + J.n2;
       L.cw8[j + 1] = L.cw8[j] + cdiv(m, 8);
-      L.crows[j + 1] = L.crows[j] + cdiv(m, 256);
+      L.crows[j + 1] = L.crows[j] + cdiv(m, 256) * cdiv(m, 64);
       L.ccols[j + 1] = L.ccols[j] + m;
       L.ctiles[j + 1] = L.ctiles[j] + (cdiv(J.n1, kGemmBM) + cdiv(J.n2, kGemmBM)) * cdiv(m, kGemmBN);
     }
@@ -205,6 +205,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.posD = c.take<int32_t>(N);
   w.rj = c.take<int32_t>(N);
   w.rk = c.take<int32_t>(N);
+  w.chain = c.take<int32_t>(N);
   w.sval = c.take<int32_t>(2 * N);
   w.colptr = c.take<const double*>(N);
   w.dcolptr = c.take<const double*>(N);
@@ -242,9 +243,9 @@ static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
   return v;
 }
 
-static void run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const tdc_opts& o,
-                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
-                     bool sign_norm, double* qa_for_sign, cudaStream_t st) {
+static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const tdc_opts& o,
+                    const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
+                    bool sign_norm, double* qa_for_sign, cudaStream_t st) {
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
               o.leaf, d, e, L.w.dmod, nvec, st);
@@ -259,13 +260,15 @@ static void run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const t
     launch_merge_level(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                        lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
                        o.max_secular_iter, st);
-    launch_product(pp, (int)li, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w,
-                   st);
+    const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(),
+                                   qb, L.w, st);
+    if (prc) return prc;
     bool any_root = false;
     for (const MergeJob& J : lv.jobs) any_root |= J.root != 0;
     launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, sign_norm && any_root, st);
   }
   (void)qa_for_sign;
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -385,7 +388,8 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   QBufs qb{Q, L.qb, L.qs};
-  run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  const int prc = run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  if (prc) return prc;
   if (profile_accounting) prof_account(P, L.w.scal, st);
   return launch_status();
 }
@@ -544,7 +548,9 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
                      qb, L.w, o.max_secular_iter, st);
-  launch_product(pp, 0, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb, L.w, st);
+  const int prc = launch_product(pp, 0, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb,
+                                 L.w, st);
+  if (prc) return prc;
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
   prof_account(P, L.w.scal, st);
@@ -616,7 +622,8 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   QBufs qb{Q_cat, L.qb, L.qs};
-  run_plan(P, pp, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
+  const int prc = run_plan(P, pp, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
+  if (prc) return prc;
   prof_account(P, L.w.scal, st);
   return launch_status();
 }

@@ -1,6 +1,7 @@
 // Product-path dispatch (see tdc_paths.cuh).
 #include <cstring>
 
+#include "tdc_hss.cuh"
 #include "tdc_ozaki.cuh"
 #include "tdc_paths.cuh"
 
@@ -13,7 +14,18 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 bool path_supported(const tdc_opts& o) {
-  return o.path == TDC_PATH_DENSE_FP64 || o.path == TDC_PATH_DENSE_OZAKI;
+  return o.path == TDC_PATH_DENSE_FP64 || o.path == TDC_PATH_DENSE_OZAKI || o.path == TDC_PATH_HSS ||
+         o.path == TDC_PATH_AUTO;
+}
+
+// Level choice: HSS for levels whose merges reach the HSS size (HSS path: two HSS
+// leaves; AUTO: k_threshold), the split product for large dense merges (split and
+// AUTO paths), FP64 otherwise.
+static int level_kind(const tdc_opts& o, int64_t maxm) {
+  if (o.path == TDC_PATH_HSS && maxm >= 2 * (int64_t)o.hss_leaf) return 2;
+  if (o.path == TDC_PATH_AUTO && maxm >= o.k_threshold) return 2;
+  if ((o.path == TDC_PATH_DENSE_OZAKI || o.path == TDC_PATH_AUTO) && maxm >= kOzMinOrder) return 1;
+  return 0;
 }
 
 void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv) {
@@ -21,16 +33,19 @@ void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::
   pp.slices = o.ozaki_slices < 5 ? 5 : (o.ozaki_slices > 7 ? 7 : o.ozaki_slices);
   pp.arena_bytes = 0;
   size_t tab = 0;
-  if (o.path != TDC_PATH_DENSE_OZAKI) {
-    pp.table_bytes = 0;
-    return;
-  }
   for (size_t l = 0; l < lv.size(); ++l) {
     const auto& jobs = *lv[l];
     int64_t maxm = 0;
     for (const MergeJob& J : jobs) maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
     PathLevel& L = pp.levels[l];
-    if (jobs.empty() || maxm < kOzMinOrder) continue;
+    if (jobs.empty()) continue;
+    const int kind = level_kind(o, maxm);
+    if (kind == 2) {
+      L.hss = true;
+      pp.arena_bytes = std::max(pp.arena_bytes, al(hss_arena_bytes(maxm, o)));
+      continue;
+    }
+    if (kind != 1) continue;
     L.oz = true;
     size_t arena = 0;
     for (const MergeJob& J : jobs) arena += al(oz_job_bytes(J, pp.slices));
@@ -49,6 +64,7 @@ bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
                const std::vector<const std::vector<MergeJob>*>& lv, cudaStream_t st) {
   pp.arena_dev = arena;
   pp.table_dev = table_dev;
+  (void)lv;
   if (pp.table_bytes == 0) return true;
   pp.table_store.assign(pp.table_bytes / 8 + 64, 0);
   pp.table = reinterpret_cast<unsigned char*>(
@@ -78,12 +94,20 @@ bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
   return ok;
 }
 
-void launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
-                    const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
-                    cudaStream_t st) {
-  (void)o;
+int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
+                   const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
+                   cudaStream_t st) {
   phase_mark(5, true, 0, st);
   const PathLevel* L = (l >= 0 && l < (int)pp.levels.size()) ? &pp.levels[l] : nullptr;
+  if (L && L->hss) {
+    int rc = 0;
+    for (const MergeJob& J : hjobs) {
+      rc = run_hss_merge(J, qb, w, pp.arena_dev, pp.arena_bytes, o, st);
+      if (rc) break;
+    }
+    phase_mark(5, false, 1, st);
+    return rc;
+  }
   if (L && L->oz) {
     const OzJob* z = reinterpret_cast<const OzJob*>(pp.table_dev + L->tab_off);
     const int64_t* c0 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[0]);
@@ -96,6 +120,7 @@ void launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vec
     launch_gemm_fp64(jobs, (int)hjobs.size(), cum_tiles, ntiles, qb, w, st);
     phase_mark(5, false, 1, st);
   }
+  return 0;
 }
 
 void launch_copy_k(const MergeScalars* scal, int64_t* k_out, cudaStream_t st) {

@@ -1,0 +1,80 @@
+// HSS form of the eigenvector product (Algorithm 1 and the HSS multiply); see hss.cu.
+#pragma once
+
+#include "../../include/tdc.h"
+#include "tdc_internal.cuh"
+
+namespace tdc {
+
+enum : int { HOP_DENSE = 0, HOP_DENSE_T = 1, HOP_QHAT = 2, HOP_QHAT_T = 3, HOP_XCOLS = 4, HOP_STACK = 5,
+             HOP_STACK_ROWS = 6 };
+enum : int { HC_DENSE = 0, HC_SCATTER = 1 };
+
+// One operand of a batched GEMM, as a logical matrix element (r, c).
+struct HOp {
+  int mode;
+  int r0, c0;                 // offsets (global Qhat indices for the generated modes)
+  const double* p;
+  int64_t ld;
+  const double* p2;           // second block (stacked modes)
+  int64_t ld2;
+  const int* split;           // device: size of the first block (stacked modes)
+  const int* ridx;            // optional index maps (generated modes)
+  const int* cidx;
+  const int* row_off_dev;     // device offset added to c0 (transposed dense mode)
+};
+
+struct HGemm {
+  int M, N, K;                // launch-time maxima
+  const int* Mdev;            // device-side actual sizes (optional)
+  const int* Ndev;
+  const int* Kdev;
+  HOp a, b;
+  int cmode;
+  double* C;
+  int64_t ldc;
+  const int32_t* cpos;        // scatter: output column of logical column c is cpos[cc0 + c]
+  int cc0;
+  double alpha, beta;
+};
+
+struct HssCols {
+  const double** col;         // kept-order columns of Q_sel
+  int32_t* type;              // row support (1: T1 rows, 2: T2 rows, 3: both)
+  int n1;
+};
+
+struct HIdJob {
+  const double* phi;          // rows x rp, column-major, leading dimension ld
+  int64_t ld;
+  int rows;                   // static row count, or
+  const int* rows_dev;        // device row count
+  int rows_max;
+  double* U;                  // rows x rank output, leading dimension rows_max
+  int* rank_out;
+  int* skel_local;
+  double* scratch;            // rp x rows_max
+};
+
+struct HssNodeDev {
+  int lo, hi, leaf, c1, c2, root;
+  double *phi, *theta;        // Phi and Theta of the node (leading dimension ldphi)
+  int64_t ldphi;
+  double *U, *V;              // leading dimension ldU
+  int64_t ldU;
+  double *Yh, *Zh, *B;        // rp x rp blocks (leading dimension rp)
+  double *G, *F;              // m x rp (multiply)
+  int *I, *J;                 // global skeleton indices
+  int *Iloc, *Jloc;           // local skeleton rows of Phi / Theta
+  int *Icand, *Jcand;         // global indices of the parent's Phi / Theta rows
+  int *kU, *kV, *rows_u, *rows_v;
+};
+
+size_t hss_arena_bytes(int64_t m, const tdc_opts& o);
+// Runs Algorithm 1 and the HSS multiply for one merge whose deflation, roots,
+// zhat and norms are in w; writes the K non-deflated output columns.  Reads K on the
+// host (one stream synchronization).  Returns 0, 3 (arena too small) or 4.
+int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, size_t arena_bytes,
+                  const tdc_opts& o, cudaStream_t st);
+
+}  // namespace tdc

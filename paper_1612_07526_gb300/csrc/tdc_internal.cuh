@@ -51,6 +51,8 @@ struct MergeScalars {
   int32_t nd;        // deflated count
   int32_t nrot;      // plane rotations applied
   int32_t sorted;    // 1 if the deflated values came out ascending
+  int32_t nchain;    // chains of rotations sharing a column
+  int32_t pad_;
   double rho;        // 2 |beta|
   double tol;        // deflation tolerance
 };
@@ -69,6 +71,7 @@ struct DevWs {
   const double **colptr;      // grouped (Gu order) non-deflated column pointers
   const double **dcolptr;     // deflated column pointers
   int32_t *rj, *rk;           // rotation records (sorted positions)
+  int32_t *chain;             // first rotation of each chain
   double *rc, *rs;
   MergeScalars *scal;         // per merge id
   double *dmod;               // torn diagonal (Eq. 2 corner updates)

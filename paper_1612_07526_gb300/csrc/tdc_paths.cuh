@@ -12,6 +12,7 @@ namespace tdc {
 
 struct PathLevel {
   bool oz = false;
+  bool hss = false;
   size_t tab_off = 0;        // OzJob array of the level in the table region
   size_t cum_off[3] = {0, 0, 0};
   int64_t nb[3] = {0, 0, 0}; // blocks: slice A, slice B, GEMM tiles
@@ -37,8 +38,8 @@ void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::
 // Binds the carved device regions, encodes the tensor maps and uploads the tables.
 bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
                const std::vector<const std::vector<MergeJob>*>& lv, cudaStream_t st);
-// Launches the product for all merges of level l.
-void launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
+// Launches the product for all merges of level l.  Returns 0, or 3 / 4 from the HSS path.
+int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
                     const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
                     cudaStream_t st);
 void launch_copy_k(const MergeScalars* scal, int64_t* k_out, cudaStream_t st);

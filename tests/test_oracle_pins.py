@@ -261,6 +261,26 @@ def test_qhat_off_diagonal_low_rank():
     assert np.linalg.norm(qh - hss.hss_to_dense(root)) <= 1e-10 * np.linalg.norm(qh)
 
 
+def test_splitmix64_published_value_and_gaussian_moments():
+    # first output of SplitMix64 seeded with 0 (the generator's published reference value)
+    assert int(hss.splitmix64(0, 0)) == 0xE220A8397B1DCDAF
+    g = hss.gaussian_matrix(7, 1, 2000, 50)
+    assert abs(g.mean()) < 0.01 and abs(g.var() - 1.0) < 0.02
+    assert not np.array_equal(g, hss.gaussian_matrix(7, 2, 2000, 50))
+
+
+def test_merge_hss_matches_dense_merge_at_tolerance():
+    """The HSS merge reproduces the dense merge to the compression tolerance; the
+    merged matrix's residual and orthogonality stay at that level."""
+    D, Q, beta = W.merge_problem(600, 600, 5)
+    lam, u, info = dc.merge(D, Q, 600, beta)
+    lam_h, u_h, info_h = dc.merge_hss(D, Q, 600, beta, leaf=128, rp=64, tol=1e-12, seed=0x5EED)
+    assert np.array_equal(lam, lam_h)
+    assert np.max(np.abs(u - u_h)) <= 1e-9
+    assert max(info_h["hss_ranks"]) < 64
+    assert np.max(np.abs(u_h.T @ u_h - np.eye(1200))) <= 1e-9
+
+
 def test_interp_decomp_exact_low_rank():
     g = W.rng(3)
     a = g.standard_normal((60, 5)) @ g.standard_normal((5, 40))
