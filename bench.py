@@ -33,6 +33,7 @@ PATHS = {"fp64": 0, "ozaki": 1, "hss": 2, "auto": 3}
 # nominal dense rates (TFLOP/s) used to scale the measured bf16 peak to FP64
 NOMINAL_BF16 = 2250.0
 NOMINAL_FP64 = 1.25
+OZAKI_PAIRS = 26        # bf16 slice products per FP64-equivalent product (6 slices, levels 2..8)
 
 
 def parse():
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=4096)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the few-deflation and batched context measurements")
     return ap.parse_args()
 
 
@@ -141,6 +144,70 @@ def cpu_oracle_sample(gen, n_full, n_s):
     except Exception:
         cores = os.cpu_count()
     return t * (n_full / n_s) ** 3, t, cores
+
+
+def profiled_solve(api, _lib, lib, torch, d, e, path, **kw):
+    """One warm-up and one timed solve with per-phase events; returns a summary."""
+    import ctypes
+    n = len(d)
+    dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
+    o = _lib.default_opts(path=PATHS[path], **kw)
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    q = api.fortran_empty(n, n, "cuda")
+    api.syev_tridiag(dt, et, opts=o, out=(lam, q))
+    torch.cuda.synchronize()
+    lib.tdc_profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.syev_tridiag(dt, et, opts=o, out=(lam, q), check=False)
+    e1.record()
+    e1.synchronize()
+    p = _lib.TdcProfile()
+    lib.tdc_profile_end(ctypes.byref(p))
+    eff = p.product_flops / (p.ms[5] * 1e-3) / 1e12 if p.ms[5] else 0.0
+    out = {"ms": e0.elapsed_time(e1), "product_ms": p.ms[5], "product_eff_fp64_tflops": eff,
+           "product_algorithmic_flops": p.product_flops}
+    if path == "ozaki":
+        out["tensor_pipe_tflops"] = eff * OZAKI_PAIRS
+    del q
+    torch.cuda.empty_cache()
+    return out
+
+
+def context_measurements(api, _lib, lib, torch):
+    """Few-deflation solves (tridiag(1,2,1), the paper's Example 2/3 matrix) with each
+    product form, and the batched configuration (ragged problems, graph replay)."""
+    import numpy as np
+    import workloads as W
+    ctx = {}
+    d, e = W.toeplitz_121(32768)
+    ctx["toeplitz_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
+    d, e = W.toeplitz_121(16384)
+    ctx["toeplitz_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64")
+    ctx["toeplitz_16384_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
+    ctx["toeplitz_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss")
+    # batched: 4096 problems, n log-uniform in [32, 2048], d, e ~ N(0, 1)
+    sizes, probs = W.batched_normal(4096, seed=0)
+    plan = api.BatchedPlan(sizes, opts={"path": PATHS["fp64"]})
+    d_cat, e_cat = plan.pack([p[0] for p in probs], [p[1] for p in probs])
+    lam, q = plan.outputs()
+    plan.capture(d_cat, e_cat, lam, q)
+    for _ in range(2):
+        plan.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        plan.replay()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
+                           "status_nonzero": int((plan.status != 0).sum())}
+    del plan, q, lam
+    torch.cuda.empty_cache()
+    return ctx
 
 
 def run_reference(args, rank):
@@ -274,6 +341,10 @@ def main():
         del hs
         torch.cuda.empty_cache()
 
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = context_measurements(api, _lib, lib, torch)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -323,6 +394,7 @@ def main():
         "product_eff_tflops": achieved,
         "accuracy": acc,
         "clocks": clk.summary(),
+        "context": extra,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -136,6 +136,23 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
                              void* stream);
 
 /*
+ * tdc_syev_tridiag_backward -- gradient of a scalar loss L(lambda, Q) with respect to
+ * (d, e), given lambda_bar = dL/dlambda and Qbar = dL/dQ at the forward output:
+ *     Tbar = Q (diag(lambda_bar) + F o (Q^T Qbar)) Q^T,  F_ic = 1/(lambda_c - lambda_i), F_ii = 0,
+ *     g_d[a] = Tbar_aa,   g_e[a] = Tbar_{a,a+1} + Tbar_{a+1,a}   (first-order perturbation
+ *     theory of the symmetric eigenproblem; distinct eigenvalues assumed).
+ * Only the band of Tbar is formed; the columns of Qbar that are entirely zero are
+ * skipped (the call synchronizes the stream once to count them).
+ *   lambda, Q (ld = ldq): the forward output;  g_lambda, g_Q (ld = ldg): may be NULL;
+ *   g_d (n), g_e (n - 1): outputs.  Workspace: tdc_backward_workspace_bytes(n, opts).
+ */
+size_t tdc_backward_workspace_bytes(int64_t n, const tdc_opts* opts);
+int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, int64_t ldq,
+                              const double* g_lambda, const double* g_Q, int64_t ldg, double* g_d,
+                              double* g_e, const tdc_opts* opts, void* ws, size_t ws_bytes,
+                              int* dev_status, void* stream);
+
+/*
  * Per-phase device timing.  Between tdc_profile_begin() and tdc_profile_end(), every
  * solve records a pair of CUDA events on its own stream around each phase of each
  * tree level, and synchronizes its stream once at its end to read back the
@@ -181,6 +198,24 @@ int tdc_profile_end(tdc_profile* out);
 #define TDC_NOALLOC_SCRATCH_BYTES (6u << 20)
 int tdc_syev_tridiag_noalloc(int64_t n, const double* d, const double* e, double* lambda,
                              double* Q, int64_t ldq, int* dev_status, void* stream);
+
+/*
+ * Batched plans for repeated solves of the same ragged shape: the DC trees, the
+ * per-level launch tables and the product path are built and uploaded once into
+ * the workspace (create synchronizes its stream); execute then only launches
+ * kernels and a status memset, so it can be captured in a CUDA graph and replayed.
+ * The problem layout is the dense packing of tdc_syev_tridiag_batched (off_de =
+ * prefix sums of n, Q blocks n_p x n_p packed back to back).  Dense product paths
+ * only (the HSS path reads sizes back to the host).  The workspace passed to create
+ * must stay alive and untouched by other calls until destroy.
+ */
+typedef struct tdc_batched_plan tdc_batched_plan;
+int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts* opts, void* ws,
+                            size_t ws_bytes, void* stream, tdc_batched_plan** out);
+int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, const double* e_cat,
+                             double* lambda_cat, double* Q_cat, int* dev_status_per_problem,
+                             void* stream);
+void tdc_batched_plan_destroy(tdc_batched_plan* plan);
 
 /* Reads a device status word on `stream` (synchronizes it).  Returns the bits. */
 int tdc_read_status(const int* dev_status, void* stream);

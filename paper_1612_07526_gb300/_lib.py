@@ -64,6 +64,13 @@ SIGNATURES = [
     ("tdc_syev_tridiag_batched", ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _OPT, _P,
                                                 ctypes.c_size_t, _P, _P]),
     ("tdc_read_status", ctypes.c_int, [_P, _P]),
+    ("tdc_backward_workspace_bytes", ctypes.c_size_t, [_I64, _OPT]),
+    ("tdc_batched_plan_create", ctypes.c_int, [ctypes.c_int32, _P, _OPT, _P, ctypes.c_size_t, _P,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
+    ("tdc_batched_plan_execute", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    ("tdc_batched_plan_destroy", None, [_P]),
+    ("tdc_syev_tridiag_backward", ctypes.c_int, [_I64, _P, _P, _I64, _P, _P, _I64, _P, _P, _OPT, _P,
+                                                 ctypes.c_size_t, _P, _P]),
     ("tdc_syev_tridiag_noalloc", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
     ("tdc_profile_begin", None, []),
     ("tdc_profile_end", ctypes.c_int, [ctypes.POINTER(TdcProfile)]),

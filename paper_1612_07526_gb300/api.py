@@ -211,3 +211,108 @@ class HostSolver:
     @property
     def d2h_bytes(self):
         return 8 * (self.n + self.n * self.n)
+
+
+def syev_backward(lam: torch.Tensor, q: torch.Tensor, g_lam=None, g_q=None, stream=None):
+    """(g_d, g_e) of a loss with gradients (g_lam, g_q) at the output (lam, q) of
+    syev_tridiag, through tdc_syev_tridiag_backward (band-only adjoint)."""
+    lib = _lib.load()
+    n = int(lam.shape[0])
+    if g_q is not None and g_q.stride() != (1, n):
+        g_q = g_q.t().contiguous().t()                 # column-major layout expected by the ABI
+    gd = torch.empty(n, dtype=torch.float64, device=lam.device)
+    ge = torch.empty(max(n - 1, 0), dtype=torch.float64, device=lam.device)
+    nb = lib.tdc_backward_workspace_bytes(n, None)
+    ws = workspace(nb, lam.device, key="backward")
+    rc = lib.tdc_syev_tridiag_backward(n, _vp(lam), _vp(q), n, _vp(g_lam), _vp(g_q), n, _vp(gd),
+                                       _vp(ge if n > 1 else None), None, _vp(ws), ws.numel(), None,
+                                       _stream(stream))
+    _check_rc(rc, "tdc_syev_tridiag_backward")
+    return gd, ge
+
+
+class TridiagEigh(torch.autograd.Function):
+    """(lam, Q) = eigh of tridiag(e, d, e) with a hand-written backward: the forward
+    saves only (lam, Q); the backward recomputes nothing of the merge tree."""
+
+    @staticmethod
+    def forward(ctx, d, e, opts=None):
+        lam, q = syev_tridiag(d.detach().contiguous(), e.detach().contiguous(), opts=opts)
+        ctx.save_for_backward(lam, q)
+        return lam, q
+
+    @staticmethod
+    def backward(ctx, g_lam, g_q):
+        lam, q = ctx.saved_tensors
+        gd, ge = syev_backward(lam, q, g_lam, g_q)
+        return gd, ge, None
+
+
+def eigh_tridiag(d: torch.Tensor, e: torch.Tensor, opts=None):
+    """Differentiable eigendecomposition of tridiag(e, d, e) (FP64, CUDA tensors)."""
+    return TridiagEigh.apply(d, e, opts)
+
+
+class BatchedPlan:
+    """A ragged batch solved repeatedly: tdc_batched_plan_create once, then
+    execute (kernel launches only) directly or from a captured CUDA graph."""
+
+    def __init__(self, sizes, opts=None, device=None):
+        self.lib = _lib.load()
+        self.sizes = np.asarray(sizes, dtype=np.int64)
+        self.o = _opts(opts)
+        dev = torch.device(device or "cuda")
+        b = len(self.sizes)
+        nb = self.lib.tdc_batched_workspace_bytes(b, self.sizes.ctypes.data_as(ctypes.c_void_p),
+                                                  ctypes.byref(self.o))
+        if nb == 0:
+            raise ValueError("invalid sizes or options")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.handle = ctypes.c_void_p()
+        rc = self.lib.tdc_batched_plan_create(b, self.sizes.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.o),
+                                              _vp(self.ws), nb, _stream(None), ctypes.byref(self.handle))
+        _check_rc(rc, "tdc_batched_plan_create")
+        self.off = np.zeros(b, dtype=np.int64)
+        self.off[1:] = np.cumsum(self.sizes)[:-1]
+        self.qoff = np.zeros(b, dtype=np.int64)
+        self.qoff[1:] = np.cumsum(self.sizes * self.sizes)[:-1]
+        self.status = torch.zeros(b, dtype=torch.int32, device=dev)
+        self.graph = None
+
+    def pack(self, ds, es, device="cuda"):
+        d_cat = torch.cat([torch.as_tensor(x, dtype=torch.float64) for x in ds]).to(device)
+        e_cat = torch.zeros(int(self.sizes.sum()), dtype=torch.float64)
+        for p, n in enumerate(self.sizes):
+            if n > 1:
+                e_cat[self.off[p]:self.off[p] + n - 1] = torch.as_tensor(es[p], dtype=torch.float64)
+        return d_cat, e_cat.to(device)
+
+    def outputs(self, device="cuda"):
+        lam = torch.empty(int(self.sizes.sum()), dtype=torch.float64, device=device)
+        q = torch.empty(int((self.sizes * self.sizes).sum()), dtype=torch.float64, device=device)
+        return lam, q
+
+    def execute(self, d_cat, e_cat, lam, q, stream=None):
+        rc = self.lib.tdc_batched_plan_execute(self.handle, _vp(d_cat), _vp(e_cat), _vp(lam), _vp(q),
+                                               _vp(self.status), _stream(stream))
+        _check_rc(rc, "tdc_batched_plan_execute")
+
+    def capture(self, d_cat, e_cat, lam, q):
+        """Captures one execute on these buffers into a CUDA graph (after a warm-up)."""
+        self.execute(d_cat, e_cat, lam, q)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.execute(d_cat, e_cat, lam, q)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.lib.tdc_batched_plan_destroy(self.handle)
+        except Exception:
+            pass

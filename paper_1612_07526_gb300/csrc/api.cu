@@ -658,6 +658,80 @@ int tdc_profile_end(tdc_profile* out) {
   return 0;
 }
 
+struct tdc_batched_plan {
+  tdc::Plan P;
+  tdc::PathPlan pp;
+  tdc::Layout L;
+  tdc_opts o;
+  int32_t batch = 0;
+  int64_t vtot = 0;
+};
+
+int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts* opts, void* ws,
+                            size_t ws_bytes, void* stream, tdc_batched_plan** out) {
+  if (batch < 1) return -1;
+  if (!n_host) return -2;
+  if (!out) return -7;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o) || o.path == TDC_PATH_HSS || o.path == TDC_PATH_AUTO) return -3;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -4;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  tdc_batched_plan* h = new tdc_batched_plan();
+  h->o = o;
+  h->batch = batch;
+  std::vector<ProblemDesc> probs(batch);
+  int64_t vtot = 0, qtot = 0;
+  for (int p = 0; p < batch; ++p) {
+    const int64_t n = n_host[p];
+    if (n < 1) {
+      delete h;
+      return -2;
+    }
+    probs[p] = ProblemDesc{n, vtot, qtot, n, qtot, n, qtot, n, -1, 0.0};
+    vtot += n;
+    qtot += n * n;
+  }
+  h->vtot = vtot;
+  build_plan(h->P, probs, o.leaf);
+  const auto lj = level_jobs(h->P);
+  path_prepare(h->pp, o, lj);
+  h->L = carve(ws, vtot, qtot, h->P.nmerges, batch, h->P.blob.size(), h->pp);
+  if (h->L.bytes > ws_bytes) {
+    delete h;
+    return 3;
+  }
+  cudaMemcpyAsync(h->L.plan, h->P.blob.data(), h->P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(h->pp, h->L.arena, h->L.table, lj, st)) {
+    delete h;
+    return 4;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    delete h;
+    return 4;
+  }
+  *out = h;
+  return 0;
+}
+
+int tdc_batched_plan_execute(const tdc_batched_plan* h, const double* d_cat, const double* e_cat,
+                             double* lambda_cat, double* Q_cat, int* dev_status_per_problem, void* stream) {
+  if (!h) return -1;
+  if (!d_cat) return -2;
+  if (!e_cat) return -3;
+  if (!lambda_cat) return -4;
+  if (!Q_cat) return -5;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L = h->L;
+  if (dev_status_per_problem) L.w.status = dev_status_per_problem;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int) * h->batch, st);
+  QBufs qb{Q_cat, L.qb, L.qs};
+  const int prc = run_plan(h->P, h->pp, L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, true, Q_cat, st);
+  if (prc) return prc;
+  return launch_status();
+}
+
+void tdc_batched_plan_destroy(tdc_batched_plan* h) { delete h; }
+
 int tdc_read_status(const int* dev_status, void* stream) {
   if (!dev_status) return -1;
   int h = 0;

@@ -541,6 +541,13 @@ HGemm gemm0() {
 
 }  // namespace
 
+void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, size_t& tab_off,
+                        cudaStream_t st) {
+  QhatSrc q{};
+  HssCols xc{};
+  launch_gemms(g, dev_tab, tab_off, q, xc, st);
+}
+
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o) {
   HssLayout L;
   hss_layout(L, nullptr, (int)m, (int)m, o);

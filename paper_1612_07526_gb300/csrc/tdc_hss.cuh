@@ -1,6 +1,8 @@
 // HSS form of the eigenvector product (Algorithm 1 and the HSS multiply); see hss.cu.
 #pragma once
 
+#include <vector>
+
 #include "../../include/tdc.h"
 #include "tdc_internal.cuh"
 
@@ -71,6 +73,9 @@ struct HssNodeDev {
 };
 
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o);
+// Batched FP64 GEMMs with dense operands only (job tables staged at dev_tab + tab_off).
+void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, size_t& tab_off,
+                        cudaStream_t st);
 // Runs Algorithm 1 and the HSS multiply for one merge whose deflation, roots,
 // zhat and norms are in w; writes the K non-deflated output columns.  Reads K on the
 // host (one stream synchronization).  Returns 0, 3 (arena too small) or 4.

@@ -128,9 +128,7 @@ void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles,
                       QBufs qb, DevWs w, cudaStream_t st);
 void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, int64_t nb_cols,
                       QBufs qb, DevWs w, bool any_root, cudaStream_t st);
-void launch_sign_normalize_batched(double* Q, const int64_t* qoff, const int64_t* nn,
-                                   const int64_t* ldd, const int64_t* cum_cols, int nprob,
-                                   int64_t ncols, cudaStream_t st);
+
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBN = 128;

@@ -261,3 +261,4 @@ def test_full_size_32768(api, gen):
     _sampled_checks(d, e, lam, q_t, cols, cols[:12])
     del q_t
     torch.cuda.empty_cache()
+
