@@ -55,7 +55,8 @@ typedef struct tdc_opts {
   int64_t k_threshold;       /* AUTO: HSS only for merges with K >= this (default 8192) */
   int32_t ozaki_slices;      /* bf16 slices per operand (default 6, range 3..8)         */
   int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
-  int32_t tile_cfg;          /* -1 = autotuned, else a fixed tile configuration index   */
+  int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
+                             /* rule), 0..4 = 128x128, 128x64, 64x64, 64x32, 32x32     */
   int32_t reserved;
 } tdc_opts;
 
@@ -159,10 +160,12 @@ int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, 
  * per-merge counts (K and the Gu groups) from which the algorithmic work of the
  * eigenvector product is counted.  Phases: 0 tear + leaves, 1 deflation + rotations,
  * 2 secular roots, 3 Loewner z + column norms, 4 eigenvalue placement,
- * 5 eigenvector product (Eq. 6), 6 deflated-column copy, 7 sign normalisation.
+ * 5 eigenvector product on the FP64 or HSS form (Eq. 6), 6 deflated-column copy,
+ * 7 sign normalisation, 8 split-precision product (the tcgen05 GEMM alone),
+ * 9 operand split of the split-precision product (digit slices of Q_sel and Qhat).
  * Not thread-safe; meant for benchmarks.
  */
-#define TDC_NPHASE 8
+#define TDC_NPHASE 10
 typedef struct tdc_profile {
   double ms[TDC_NPHASE];           /* summed event time per phase                     */
   int64_t launches[TDC_NPHASE];    /* kernel launches per phase                       */
@@ -172,6 +175,10 @@ typedef struct tdc_profile {
   int64_t merges;                  /* merges executed                                 */
   int64_t K_total;                 /* sum of K over merges                            */
   int64_t calls;                   /* solves recorded                                 */
+  double fp64_product_flops;       /* product_flops of the merges on the FP64 product */
+  double split_product_flops;      /* product_flops of the merges on the split product */
+  double split_tensor_flops;       /* bf16 tensor flops those run: slice pairs x 2 m K K */
+  double defl_copy_bytes;          /* 16 bytes x rows x deflated columns over merges   */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);
@@ -216,6 +223,30 @@ int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, 
                              double* lambda_cat, double* Q_cat, int* dev_status_per_problem,
                              void* stream);
 void tdc_batched_plan_destroy(tdc_batched_plan* plan);
+
+/*
+ * Autotuning of the FP64 product's tile shape per DC tree level (the five shapes of
+ * tdc_opts.tile_cfg).  Every FP64 product sums each output element over k in the
+ * same order whatever the shape, so the shape changes speed, never results.
+ *
+ * tdc_autotune -- runs the full solve of this input once per shape, twice over,
+ * times each level's product with CUDA events on `stream`, and records the fastest
+ * shape per level in a process-wide table keyed by the tree's level structure;
+ * later calls on trees of that structure with tile_cfg == -1 use it.  Arguments as
+ * for tdc_syev_tridiag (lambda and Q receive a valid solve).  shape_per_level
+ * (nullable, max_levels entries) receives the chosen shapes, leaves to root,
+ * and *n_levels (nullable) the number of levels.  Synchronizes `stream`.
+ * Returns 0, -i for a bad argument i, 3 (workspace) or 4 (device error).
+ *
+ * tdc_batched_plan_autotune -- the same for a batched plan: the plan's own shapes are
+ * replaced by the tuned ones (so tune before capturing execute in a graph).
+ */
+int tdc_autotune(int64_t n, const double* d, const double* e, double* lambda, double* Q, int64_t ldq,
+                 const tdc_opts* opts, void* ws, size_t ws_bytes, int32_t* shape_per_level,
+                 int32_t max_levels, int32_t* n_levels, int* dev_status, void* stream);
+int tdc_batched_plan_autotune(tdc_batched_plan* plan, const double* d_cat, const double* e_cat,
+                              double* lambda_cat, double* Q_cat, int32_t* shape_per_level,
+                              int32_t max_levels, int32_t* n_levels, void* stream);
 
 /* Reads a device status word on `stream` (synchronizes it).  Returns the bits. */
 int tdc_read_status(const int* dev_status, void* stream);

@@ -32,18 +32,22 @@ class TdcOpts(ctypes.Structure):
 
 class TdcProfile(ctypes.Structure):
     _fields_ = [
-        ("ms", ctypes.c_double * 8),
-        ("launches", ctypes.c_int64 * 8),
+        ("ms", ctypes.c_double * 10),
+        ("launches", ctypes.c_int64 * 10),
         ("product_flops", ctypes.c_double),
         ("product_min_bytes", ctypes.c_double),
         ("merges", ctypes.c_int64),
         ("K_total", ctypes.c_int64),
         ("calls", ctypes.c_int64),
+        ("fp64_product_flops", ctypes.c_double),
+        ("split_product_flops", ctypes.c_double),
+        ("split_tensor_flops", ctypes.c_double),
+        ("defl_copy_bytes", ctypes.c_double),
     ]
 
 
 PHASES = ["tear+leaves", "deflation", "secular", "lowner+norms", "placement", "product",
-          "deflated-copy", "sign"]
+          "deflated-copy", "sign", "split-product", "operand-split"]
 
 _lib = None
 
@@ -72,10 +76,17 @@ SIGNATURES = [
     ("tdc_syev_tridiag_backward", ctypes.c_int, [_I64, _P, _P, _I64, _P, _P, _I64, _P, _P, _OPT, _P,
                                                  ctypes.c_size_t, _P, _P]),
     ("tdc_syev_tridiag_noalloc", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
+    ("tdc_autotune", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _OPT, _P, ctypes.c_size_t, _P, ctypes.c_int32,
+                                    _P, _P, _P]),
+    ("tdc_batched_plan_autotune", ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P, _P]),
     ("tdc_profile_begin", None, []),
     ("tdc_profile_end", ctypes.c_int, [ctypes.POINTER(TdcProfile)]),
     ("tdc_version", ctypes.c_char_p, []),
 ]
+
+
+# FP64 product tile shapes (rows, columns) by tdc_opts.tile_cfg index
+TILE_SHAPES = [(128, 128), (128, 64), (64, 64), (64, 32), (32, 32)]
 
 
 def load(path: str = LIB_PATH):

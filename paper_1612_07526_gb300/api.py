@@ -108,6 +108,31 @@ def syev_tridiag(d: torch.Tensor, e: torch.Tensor, opts=None, stream=None, check
     return lam, q
 
 
+def autotune(d: torch.Tensor, e: torch.Tensor, opts=None, stream=None):
+    """Times every FP64 product tile shape per tree level on this input
+    (tdc_autotune) and records the fastest; later solves of the same tree structure
+    with tile_cfg = -1 use it.  Returns the shape index per level (leaves to root)."""
+    lib = _lib.load()
+    n = int(d.shape[0])
+    assert d.dtype == torch.float64 and d.is_cuda and d.is_contiguous()
+    assert e.dtype == torch.float64 and e.is_cuda and e.is_contiguous() and e.shape[0] == max(n - 1, 0)
+    o = _opts(opts)
+    lam = torch.empty(n, dtype=torch.float64, device=d.device)
+    q = fortran_empty(n, n, d.device)
+    nb = lib.tdc_workspace_bytes(n, ctypes.byref(o))
+    if nb == 0:
+        raise ValueError("invalid size or options")
+    ws = workspace(nb, d.device)
+    st = torch.zeros(1, dtype=torch.int32, device=d.device)
+    shapes = (ctypes.c_int32 * 64)()
+    nl = ctypes.c_int32(0)
+    rc = lib.tdc_autotune(n, _vp(d), _vp(e if n > 1 else None), _vp(lam), _vp(q), n, ctypes.byref(o), _vp(ws),
+                          ws.numel(), shapes, 64, ctypes.byref(nl), _vp(st), _stream(stream))
+    _check_rc(rc, "tdc_autotune")
+    _raise_status(lib.tdc_read_status(_vp(st), _stream(stream)), "tdc_autotune")
+    return [int(shapes[i]) for i in range(min(nl.value, 64))]
+
+
 def merge(D: torch.Tensor, Q: torch.Tensor, n1: int, beta: float, opts=None, stream=None,
           check: bool = True):
     """One rank-one merge (Eqs. 3-6) of diag(Q1 D1 Q1^T, Q2 D2 Q2^T) + |beta| v v^T.
@@ -296,6 +321,16 @@ class BatchedPlan:
         rc = self.lib.tdc_batched_plan_execute(self.handle, _vp(d_cat), _vp(e_cat), _vp(lam), _vp(q),
                                                _vp(self.status), _stream(stream))
         _check_rc(rc, "tdc_batched_plan_execute")
+
+    def autotune(self, d_cat, e_cat, lam, q, stream=None):
+        """Tunes the plan's FP64 product tile shape per level (before capture).
+        Returns the shape index per level."""
+        shapes = (ctypes.c_int32 * 64)()
+        nl = ctypes.c_int32(0)
+        rc = self.lib.tdc_batched_plan_autotune(self.handle, _vp(d_cat), _vp(e_cat), _vp(lam), _vp(q), shapes, 64,
+                                                ctypes.byref(nl), _stream(stream))
+        _check_rc(rc, "tdc_batched_plan_autotune")
+        return [int(shapes[i]) for i in range(min(nl.value, 64))]
 
     def capture(self, d_cat, e_cat, lam, q):
         """Captures one execute on these buffers into a CUDA graph (after a warm-up)."""

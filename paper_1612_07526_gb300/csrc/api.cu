@@ -8,6 +8,7 @@
 
 #include "../../include/tdc.h"
 #include "tdc_internal.cuh"
+#include "tdc_ozaki.cuh"
 #include "tdc_paths.cuh"
 
 namespace tdc {
@@ -107,7 +108,7 @@ static void finish_plan(Plan& P) {
       L.cw8[j + 1] = L.cw8[j] + cdiv(m, 8);
       L.crows[j + 1] = L.crows[j] + cdiv(m, 256) * cdiv(m, 64);
       L.ccols[j + 1] = L.ccols[j] + m;
-      L.ctiles[j + 1] = L.ctiles[j] + (cdiv(J.n1, kGemmBM) + cdiv(J.n2, kGemmBM)) * cdiv(m, kGemmBN);
+      // ctiles is device scratch: the product rewrites it from the actual K
     }
   }
   P.blob.clear();
@@ -169,7 +170,7 @@ struct Layout {
 };
 
 static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int nprob,
-                    size_t plan_bytes, const PathPlan& ps) {
+                    size_t plan_bytes, const PathPlan& ps, int64_t nleaf) {
   Carver c{reinterpret_cast<unsigned char*>(ws)};
   Layout L;
   const size_t N = (size_t)std::max<int64_t>(nvec, 1);
@@ -210,6 +211,10 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.colptr = c.take<const double*>(N);
   w.dcolptr = c.take<const double*>(N);
   w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
+  const size_t NL = (size_t)std::max<int64_t>(nleaf, 1);
+  w.lrot = c.take<double2>(NL * kLeafRot);
+  w.lroti = c.take<uint8_t>(NL * kLeafRot);
+  w.lrotn = c.take<int32_t>(NL);
   w.status = c.take<int>((size_t)std::max(nprob, 1));
   L.plan = c.take<unsigned char>(plan_bytes);
   L.table = c.take<unsigned char>(ps.table_bytes);
@@ -235,6 +240,10 @@ template <class T>
 static const T* P_(const Layout& L, size_t off) {
   return reinterpret_cast<const T*>(L.plan + off);
 }
+template <class T>
+static T* PM_(const Layout& L, size_t off) {        // device scratch inside the plan region
+  return reinterpret_cast<T*>(L.plan + off);
+}
 
 // Launch the whole level sequence of a plan whose blob is already on the device.
 static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
@@ -249,9 +258,8 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
               o.leaf, d, e, L.w.dmod, nvec, st);
-  launch_leaves(P_<LeafJob>(L, P.o_leaves), (int)P.leaves.size(), L.w.dmod, e, lam, qb,
-                L.w.status, st);
-  phase_mark(0, false, 3, st);
+  launch_leaves(P_<LeafJob>(L, P.o_leaves), (int)P.leaves.size(), L.w.dmod, e, lam, qb, L.w, st);
+  phase_mark(0, false, 4, st);
   for (size_t li = 0; li < P.levels.size(); ++li) {
     const LevelPlan& lv = P.levels[li];
     const int nj = (int)lv.jobs.size();
@@ -260,8 +268,7 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
     launch_merge_level(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                        lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
                        o.max_secular_iter, st);
-    const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(),
-                                   qb, L.w, st);
+    const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
     if (prc) return prc;
     bool any_root = false;
     for (const MergeJob& J : lv.jobs) any_root |= J.root != 0;
@@ -269,6 +276,73 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
   }
   (void)qa_for_sign;
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the FP64 product tile shape per tree level: the whole plan runs
+// once per shape (every FP64-product level on that shape), each level's product is
+// timed with CUDA events, best of two rounds, and the fastest shape per level is
+// kept in the plan and recorded for plans of the same level structure.  All shapes
+// give bit-identical results, so tuning changes speed only.
+// ---------------------------------------------------------------------------
+static int autotune_plan(const Plan& P, PathPlan& pp, const Layout& L, const tdc_opts& o, const double* d,
+                         const double* e, double* lam, QBufs qb, int64_t nvec, int nprob, cudaStream_t st,
+                         std::vector<int>& best) {
+  const int nl = (int)P.levels.size();
+  LevelTimer T;
+  T.a.assign(nl, nullptr);
+  T.b.assign(nl, nullptr);
+  T.used.assign(nl, false);
+  for (int l = 0; l < nl; ++l) {
+    cudaEventCreate(&T.a[l]);
+    cudaEventCreate(&T.b[l]);
+  }
+  std::vector<std::vector<float>> t(kGemmShapes, std::vector<float>(nl, 3.0e38f));
+  std::vector<int> keep(nl);
+  for (int l = 0; l < nl; ++l) keep[l] = pp.levels[l].gemm_cfg;
+  std::vector<bool> timed(nl, false);
+  int rc = 0;
+  for (int rep = 0; rep < 2 && rc == 0; ++rep) {
+    for (int c = 0; c < kGemmShapes && rc == 0; ++c) {
+      for (int l = 0; l < nl; ++l) path_set_shape(pp, l, c, P.levels[l].jobs);
+      std::fill(T.used.begin(), T.used.end(), false);
+      cudaMemsetAsync(L.w.status, 0, sizeof(int) * std::max(nprob, 1), st);
+      set_level_timer(&T);
+      rc = run_plan(P, pp, L, o, d, e, lam, qb, nvec, nprob, true, nullptr, st);
+      set_level_timer(nullptr);
+      if (rc == 0 && cudaStreamSynchronize(st) != cudaSuccess) rc = 4;
+      if (rc) break;
+      for (int l = 0; l < nl; ++l) {
+        if (!T.used[l]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, T.a[l], T.b[l]) == cudaSuccess) t[c][l] = std::min(t[c][l], ms);
+        timed[l] = true;
+      }
+    }
+  }
+  best.assign(nl, 0);
+  for (int l = 0; l < nl; ++l) {
+    int b = keep[l];
+    if (timed[l]) {
+      b = 0;
+      for (int c = 1; c < kGemmShapes; ++c)
+        if (t[c][l] < t[b][l]) b = c;
+    }
+    best[l] = b;
+    path_set_shape(pp, l, b, P.levels[l].jobs);
+  }
+  for (int l = 0; l < nl; ++l) {
+    cudaEventDestroy(T.a[l]);
+    cudaEventDestroy(T.b[l]);
+  }
+  if (rc == 0) tune_store(tune_key(o, level_jobs(P)), best);
+  return rc;
+}
+
+static void copy_shapes(const std::vector<int>& best, int32_t* out, int32_t max_levels, int32_t* n_out) {
+  if (n_out) *n_out = (int32_t)best.size();
+  if (!out) return;
+  for (int l = 0; l < (int)best.size() && l < max_levels; ++l) out[l] = best[l];
 }
 
 // ---------------------------------------------------------------------------
@@ -285,7 +359,7 @@ struct ProfState {
   std::vector<ProfRec> recs;
   cudaEvent_t open_ev = nullptr;
   int64_t launches[TDC_NPHASE] = {};
-  double flops = 0.0, bytes = 0.0;
+  double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   int64_t merges = 0, ktot = 0, calls = 0;
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
@@ -315,7 +389,7 @@ void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
 }
 
 // After a profiled solve: read the per-merge counts and add up the product's work.
-static void prof_account(const Plan& P, const MergeScalars* dscal, cudaStream_t st) {
+static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* dscal, cudaStream_t st) {
   if (!g_prof.on) return;
   const size_t nm = (size_t)std::max<int64_t>(P.nmerges, 1);
   if (g_prof.hscal_n < nm) {
@@ -325,15 +399,28 @@ static void prof_account(const Plan& P, const MergeScalars* dscal, cudaStream_t 
   }
   cudaMemcpyAsync(g_prof.hscal, dscal, nm * sizeof(MergeScalars), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  for (const LevelPlan& lv : P.levels)
-    for (const MergeJob& J : lv.jobs) {
+  const double pairs = oz_slice_pairs(pp.slices);
+  for (size_t l = 0; l < P.levels.size(); ++l) {
+    const bool oz = l < pp.levels.size() && pp.levels[l].oz;
+    const bool hss = l < pp.levels.size() && pp.levels[l].hss;
+    for (const MergeJob& J : P.levels[l].jobs) {
       const MergeScalars& S = g_prof.hscal[J.mid];
       const double K = S.K, c1 = S.c1, c3 = S.c3, c2 = S.K - S.c1 - S.c3;
-      g_prof.flops += 2.0 * K * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2));
-      g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + (double)(J.n1 + J.n2) * K);
+      const double m = (double)J.n1 + J.n2;
+      const double f = 2.0 * K * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2));
+      g_prof.flops += f;
+      if (oz) {
+        g_prof.split_flops += f;
+        g_prof.tensor_flops += pairs * f;
+      } else if (!hss) {
+        g_prof.fp64_flops += f;
+      }
+      g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
+      g_prof.copy_bytes += 16.0 * m * (m - K);
       g_prof.merges += 1;
       g_prof.ktot += S.K;
     }
+  }
   g_prof.calls += 1;
 }
 
@@ -359,7 +446,7 @@ static void single_problem_plan(Plan& P, int64_t n, int64_t ldq, int leaf) {
 static size_t syev_bytes(int64_t n, const tdc_opts& o, const Plan& P) {
   PathPlan pp;
   path_prepare(pp, o, level_jobs(P));
-  Layout L = carve(nullptr, n, n * n, P.nmerges, 1, P.blob.size(), pp);
+  Layout L = carve(nullptr, n, n * n, P.nmerges, 1, P.blob.size(), pp, (int64_t)P.leaves.size());
   return L.bytes;
 }
 
@@ -381,7 +468,7 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   PathPlan pp;
   const auto lj = level_jobs(P);
   path_prepare(pp, o, lj);
-  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp);
+  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp, (int64_t)P.leaves.size());
   if (L.bytes > ws_bytes) return 3;
   if (dev_status) L.w.status = dev_status;
   cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
@@ -390,7 +477,7 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   QBufs qb{Q, L.qb, L.qs};
   const int prc = run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
   if (prc) return prc;
-  if (profile_accounting) prof_account(P, L.w.scal, st);
+  if (profile_accounting) prof_account(P, pp, L.w.scal, st);
   return launch_status();
 }
 
@@ -430,6 +517,38 @@ int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda
                      int64_t ldq, const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
                      void* stream) {
   return tdc::syev_core(n, d, e, lambda, Q, ldq, opts, ws, ws_bytes, dev_status, stream, true);
+}
+
+int tdc_autotune(int64_t n, const double* d, const double* e, double* lambda, double* Q, int64_t ldq,
+                 const tdc_opts* opts, void* ws, size_t ws_bytes, int32_t* shape_per_level,
+                 int32_t max_levels, int32_t* n_levels, int* dev_status, void* stream) {
+  if (n < 1) return -1;
+  if (!d) return -2;
+  if (!e && n > 1) return -3;
+  if (!lambda) return -4;
+  if (!Q) return -5;
+  if (ldq < n) return -6;
+  const tdc_opts o = resolve_opts(opts);
+  if (!opts_valid(o) || !path_supported(o)) return -7;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -8;
+  if (shape_per_level && max_levels < 0) return -11;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  single_problem_plan(P, n, ldq, o.leaf);
+  PathPlan pp;
+  const auto lj = level_jobs(P);
+  path_prepare(pp, o, lj);
+  Layout L = carve(ws, n, n * n, P.nmerges, 1, P.blob.size(), pp, (int64_t)P.leaves.size());
+  if (L.bytes > ws_bytes) return 3;
+  if (dev_status) L.w.status = dev_status;
+  cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
+  if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
+  QBufs qb{Q, L.qb, L.qs};
+  std::vector<int> best;
+  const int rc = autotune_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, st, best);
+  if (rc) return rc;
+  copy_shapes(best, shape_per_level, max_levels, n_levels);
+  return launch_status();
 }
 
 size_t tdc_host_buffer_bytes(int64_t n, const tdc_opts* opts) {
@@ -490,7 +609,7 @@ size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts) {
   finish_plan(P);
   PathPlan pp;
   path_prepare(pp, o, level_jobs(P));
-  Layout L = carve(nullptr, n, n * n, 1, 1, P.blob.size(), pp);
+  Layout L = carve(nullptr, n, n * n, 1, 1, P.blob.size(), pp, 0);
   return L.bytes;
 }
 
@@ -535,7 +654,7 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   PathPlan pp;
   const auto lj = level_jobs(P);
   path_prepare(pp, o, lj);
-  Layout L = carve(ws, n, n * n, 1, 1, P.blob.size(), pp);
+  Layout L = carve(ws, n, n * n, 1, 1, P.blob.size(), pp, 0);
   if (L.bytes > ws_bytes) return 3;
   if (dev_status) L.w.status = dev_status;
   cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
@@ -548,12 +667,11 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
                      qb, L.w, o.max_secular_iter, st);
-  const int prc = launch_product(pp, 0, o, lv.jobs, jobs, P_<int64_t>(L, lv.o_ctiles), lv.ctiles.back(), qb,
-                                 L.w, st);
+  const int prc = launch_product(pp, 0, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
   if (prc) return prc;
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
-  prof_account(P, L.w.scal, st);
+  prof_account(P, pp, L.w.scal, st);
   return launch_status();
 }
 
@@ -574,7 +692,7 @@ size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const t
   build_plan(P, probs, o.leaf);
   PathPlan pp;
   path_prepare(pp, o, level_jobs(P));
-  Layout L = carve(nullptr, vtot, qtot, P.nmerges, batch, P.blob.size(), pp);
+  Layout L = carve(nullptr, vtot, qtot, P.nmerges, batch, P.blob.size(), pp, (int64_t)P.leaves.size());
   return L.bytes;
 }
 
@@ -615,7 +733,7 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
   PathPlan pp;
   const auto lj = level_jobs(P);
   path_prepare(pp, o, lj);
-  Layout L = carve(ws, vtot, qtot, P.nmerges, batch, P.blob.size(), pp);
+  Layout L = carve(ws, vtot, qtot, P.nmerges, batch, P.blob.size(), pp, (int64_t)P.leaves.size());
   if (L.bytes > ws_bytes) return 3;
   if (dev_status_per_problem) L.w.status = dev_status_per_problem;
   cudaMemsetAsync(L.w.status, 0, sizeof(int) * batch, st);
@@ -624,7 +742,7 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
   QBufs qb{Q_cat, L.qb, L.qs};
   const int prc = run_plan(P, pp, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
   if (prc) return prc;
-  prof_account(P, L.w.scal, st);
+  prof_account(P, pp, L.w.scal, st);
   return launch_status();
 }
 
@@ -633,7 +751,8 @@ void tdc_profile_begin(void) {
   g_prof.used = 0;
   g_prof.recs.clear();
   for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
-  g_prof.flops = g_prof.bytes = 0.0;
+  g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
+  g_prof.copy_bytes = 0.0;
   g_prof.merges = g_prof.ktot = g_prof.calls = 0;
 }
 
@@ -652,6 +771,10 @@ int tdc_profile_end(tdc_profile* out) {
   out->merges = g_prof.merges;
   out->K_total = g_prof.ktot;
   out->calls = g_prof.calls;
+  out->fp64_product_flops = g_prof.fp64_flops;
+  out->split_product_flops = g_prof.split_flops;
+  out->split_tensor_flops = g_prof.tensor_flops;
+  out->defl_copy_bytes = g_prof.copy_bytes;
   g_prof.on = false;
   g_prof.recs.clear();
   g_prof.used = 0;
@@ -695,7 +818,7 @@ int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts
   build_plan(h->P, probs, o.leaf);
   const auto lj = level_jobs(h->P);
   path_prepare(h->pp, o, lj);
-  h->L = carve(ws, vtot, qtot, h->P.nmerges, batch, h->P.blob.size(), h->pp);
+  h->L = carve(ws, vtot, qtot, h->P.nmerges, batch, h->P.blob.size(), h->pp, (int64_t)h->P.leaves.size());
   if (h->L.bytes > ws_bytes) {
     delete h;
     return 3;
@@ -727,6 +850,24 @@ int tdc_batched_plan_execute(const tdc_batched_plan* h, const double* d_cat, con
   QBufs qb{Q_cat, L.qb, L.qs};
   const int prc = run_plan(h->P, h->pp, L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, true, Q_cat, st);
   if (prc) return prc;
+  return launch_status();
+}
+
+int tdc_batched_plan_autotune(tdc_batched_plan* h, const double* d_cat, const double* e_cat,
+                              double* lambda_cat, double* Q_cat, int32_t* shape_per_level, int32_t max_levels,
+                              int32_t* n_levels, void* stream) {
+  if (!h) return -1;
+  if (!d_cat) return -2;
+  if (!e_cat) return -3;
+  if (!lambda_cat) return -4;
+  if (!Q_cat) return -5;
+  if (shape_per_level && max_levels < 0) return -7;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  QBufs qb{Q_cat, h->L.qb, h->L.qs};
+  std::vector<int> best;
+  const int rc = autotune_plan(h->P, h->pp, h->L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, st, best);
+  if (rc) return rc;
+  copy_shapes(best, shape_per_level, max_levels, n_levels);
   return launch_status();
 }
 

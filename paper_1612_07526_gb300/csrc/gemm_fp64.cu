@@ -7,17 +7,29 @@
 // use the first two groups and rows of T2 the last two, so the zero blocks of
 // diag(Q1, Q2) are never multiplied.  Qhat is never stored.
 //
-// Tile 128 x 128 x 8, 256 threads, 8 x 8 FP64 accumulators per thread,
-// double-buffered shared memory; the next tile of Qhat is generated while the
-// current one is consumed.
+// Tile shapes BM x BN x 8 (BM, BN in {32, 64, 128}), 256 threads in a 16 x 16 grid,
+// (BM/16) x (BN/16) FP64 accumulators per thread, double-buffered shared memory;
+// the next slab of Qhat is generated while the current one is consumed.  Every
+// output element is one FMA chain over k in ascending order, whatever the shape,
+// so all shapes give bit-identical results and the shape is a pure speed choice.
+//
+// Scheduling: K is known only on the device, so a one-block kernel first counts
+// each merge's tiles from its K (k_gemm_sched) and the product kernel strides over
+// exactly those tiles; tiles beyond K are never visited.
 #include "tdc_internal.cuh"
 
 namespace tdc {
 
 namespace {
 
-constexpr int BM = kGemmBM, BN = kGemmBN, BK = 8, NT = 256;
+constexpr int BK = 8, NT = 256;
 
+struct Shape {
+  int bm, bn;
+};
+constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32}, {32, 32}};
+
+template <int BM, int BN>
 struct GemmSmem {
   double As[2][BK][BM];
   double Bs[2][BK][BN];
@@ -25,14 +37,13 @@ struct GemmSmem {
   int pos[BN];
 };
 
-__device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJob* __restrict__ jobs,
+template <int BM, int BN>
+__device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, const MergeJob* __restrict__ jobs,
                                           int njobs, const int64_t* __restrict__ cum, QBufs qb, DevWs w) {
+  constexpr int TM = BM / 16, TN = BN / 16;         // accumulators per thread
+  constexpr int LA = BM * BK / NT, LB = BN * BK / NT; // loads / generated entries per thread
   auto& As = sm.As;
   auto& Bs = sm.Bs;
-  double* s_dorg = sm.dorg;
-  double* s_tau = sm.tau;
-  double* s_sinv = sm.sinv;
-  int* s_pos = sm.pos;
   const int jb = find_job(cum, njobs, vb);
   const MergeJob J = jobs[jb];
   const int64_t tile = vb - cum[jb];
@@ -42,7 +53,6 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJ
   const int rt = (int)(tile % (nrt1 + nrt2));
   const MergeScalars S = w.scal[J.mid];
   const int K = S.K;
-  if (ct * BN >= K) return;
   const bool top = rt < nrt1;
   const int r0 = top ? rt * BM : n1 + (rt - nrt1) * BM;
   const int rend = top ? n1 : m;
@@ -58,63 +68,62 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJ
   for (int c = tid; c < BN; c += NT) {
     const int i = ct * BN + c;
     if (i < K) {
-      s_dorg[c] = dbar[w.org[o + i]];
-      s_tau[c] = w.tau[o + i];
-      s_sinv[c] = w.sinv[o + i];
-      s_pos[c] = w.posK[o + i];
+      sm.dorg[c] = dbar[w.org[o + i]];
+      sm.tau[c] = w.tau[o + i];
+      sm.sinv[c] = w.sinv[o + i];
+      sm.pos[c] = w.posK[o + i];
     } else {
-      s_dorg[c] = 0.0;
-      s_tau[c] = 0.0;
-      s_sinv[c] = 0.0;
-      s_pos[c] = -1;
+      sm.dorg[c] = 0.0;
+      sm.tau[c] = 0.0;
+      sm.sinv[c] = 0.0;
+      sm.pos[c] = -1;
     }
   }
   __syncthreads();
 
-  // loader mapping: 8 rows of k, 32 threads x 4 consecutive rows / columns each
-  const int lk = tid >> 5;
-  const int l4 = (tid & 31) * 4;
-  double ra[4], rb[4];
+  // loader mapping: thread t covers LA consecutive rows (LB columns) of one k row
+  const int la_k = (tid * LA) / BM, la_r = (tid * LA) % BM;
+  const int lb_k = (tid * LB) / BN, lb_c = (tid * LB) % BN;
+  double ra[LA], rb[LB];
   auto load_a = [&](int k0) {
-    const int k = k0 + lk;
+    const int k = k0 + la_k;
     if (k < kend) {
       const double* col = colptr[k] + r0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ra[u] = (r0 + l4 + u < rend) ? col[l4 + u] : 0.0;
+      for (int u = 0; u < LA; ++u) ra[u] = (r0 + la_r + u < rend) ? col[la_r + u] : 0.0;
     } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ra[u] = 0.0;
+      for (int u = 0; u < LA; ++u) ra[u] = 0.0;
     }
   };
   auto gen_b = [&](int k0) {
-    const int k = k0 + lk;
+    const int k = k0 + lb_k;
     if (k < kend) {
       const int j = kperm[k];
       const double zj = zhat[j], dj = dbar[j];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = l4 + u;
-        rb[u] = (s_pos[c] >= 0) ? (zj / ((dj - s_dorg[c]) - s_tau[c])) * s_sinv[c] : 0.0;
+      for (int u = 0; u < LB; ++u) {
+        const int c = lb_c + u;
+        rb[u] = (sm.pos[c] >= 0) ? (zj / ((dj - sm.dorg[c]) - sm.tau[c])) * sm.sinv[c] : 0.0;
       }
     } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) rb[u] = 0.0;
+      for (int u = 0; u < LB; ++u) rb[u] = 0.0;
     }
   };
   auto store = [&](int stg) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      As[stg][lk][l4 + u] = ra[u];
-      Bs[stg][lk][l4 + u] = rb[u];
-    }
+    for (int u = 0; u < LA; ++u) As[stg][la_k][la_r + u] = ra[u];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) Bs[stg][lb_k][lb_c + u] = rb[u];
   };
 
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[8][8];
+  double acc[TM][TN];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
 
   if (kbeg < kend) {
     load_a(kbeg);
@@ -127,15 +136,15 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJ
       if (more) load_a(k0 + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double fa[8], fb[8];
+        double fa[TM], fb[TN];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) fa[a] = As[stg][kk][tx + 16 * a];
+        for (int a = 0; a < TM; ++a) fa[a] = As[stg][kk][tx + 16 * a];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) fb[b] = Bs[stg][kk][ty + 16 * b];
+        for (int b = 0; b < TN; ++b) fb[b] = Bs[stg][kk][ty + 16 * b];
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < TM; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = fma(fa[a], fb[b], acc[a][b]);
+          for (int b = 0; b < TN; ++b) acc[a][b] = fma(fa[a], fb[b], acc[a][b]);
       }
       if (more) {
         gen_b(k0 + BK);
@@ -146,40 +155,96 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem& sm, const MergeJ
     }
   }
 
-  int64_t ld;
   double* out = (J.src ? qb.A + J.off_a : qb.B + J.off_b);
-  ld = J.src ? J.lda : J.ldb;
+  const int64_t ld = J.src ? J.lda : J.ldb;
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
+  for (int b = 0; b < TN; ++b) {
     const int c = ty + 16 * b;
-    const int pos = s_pos[c];
+    const int pos = sm.pos[c];
     if (pos < 0) continue;
     double* col = out + (int64_t)pos * ld + r0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
+    for (int a = 0; a < TM; ++a) {
       const int r = tx + 16 * a;
       if (r0 + r < rend) col[r] = acc[a][b];
     }
   }
 }
 
-// Grid-stride over the level's tiles: tiles of columns beyond K cost a few loads.
-__global__ __launch_bounds__(NT) void k_gemm_fp64(int64_t ntiles, const MergeJob* __restrict__ jobs,
-                                                  int njobs, const int64_t* __restrict__ cum, QBufs qb,
-                                                  DevWs w) {
-  __shared__ GemmSmem sm;
+// Tiles of each merge from its actual K: (row tiles of T1 + of T2) x ceil(K / BN);
+// cum[j] = tiles of merges before j.  One block; thread t sums a contiguous run of
+// merges, then the runs are scanned in shared memory.
+__global__ __launch_bounds__(1024) void k_gemm_sched(const MergeJob* __restrict__ jobs, int njobs,
+                                                     const MergeScalars* __restrict__ scal, int bm, int bn,
+                                                     int64_t* __restrict__ cum) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (njobs + 1023) / 1024;
+  const int j0 = min(t * per, njobs), j1 = min(j0 + per, njobs);
+  int64_t s = 0;
+  for (int j = j0; j < j1; ++j) {
+    const MergeJob& J = jobs[j];
+    const int K = scal[J.mid].K;
+    s += (int64_t)((J.n1 + bm - 1) / bm + (J.n2 + bm - 1) / bm) * ((K + bn - 1) / bn);
+  }
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {      // inclusive Hillis-Steele scan
+    const int64_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = t > 0 ? part[t - 1] : 0;
+  for (int j = j0; j < j1; ++j) {
+    cum[j] = run;
+    const MergeJob& J = jobs[j];
+    const int K = scal[J.mid].K;
+    run += (int64_t)((J.n1 + bm - 1) / bm + (J.n2 + bm - 1) / bm) * ((K + bn - 1) / bn);
+  }
+  if (t == 1023) cum[njobs] = part[1023];
+}
+
+template <int BM, int BN>
+__global__ __launch_bounds__(NT) void k_gemm_fp64(const MergeJob* __restrict__ jobs, int njobs,
+                                                  const int64_t* __restrict__ cum, QBufs qb, DevWs w) {
+  __shared__ GemmSmem<BM, BN> sm;
+  const int64_t ntiles = cum[njobs];
   for (int64_t vb = blockIdx.x; vb < ntiles; vb += gridDim.x) {
-    gemm_tile(vb, sm, jobs, njobs, cum, qb, w);
+    gemm_tile<BM, BN>(vb, sm, jobs, njobs, cum, qb, w);
     __syncthreads();
   }
 }
 
+template <int BM, int BN>
+void launch_shape(const MergeJob* jobs, int njobs, int64_t* cum, int64_t bound, QBufs qb, DevWs w,
+                  cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_fp64<BM, BN>, NT, 0) != cudaSuccess || b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  k_gemm_sched<<<1, 1024, 0, st>>>(jobs, njobs, w.scal, BM, BN, cum);
+  k_gemm_fp64<BM, BN><<<grid_cap(bound, per_sm), NT, 0, st>>>(jobs, njobs, cum, qb, w);
+}
+
 }  // namespace
 
-void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles, int64_t ntiles,
+int gemm_shape_rows(int cfg) { return kShapes[cfg].bm; }
+int gemm_shape_cols(int cfg) { return kShapes[cfg].bn; }
+
+void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_tiles, int64_t bound,
                       QBufs qb, DevWs w, cudaStream_t st) {
-  if (ntiles == 0) return;
-  k_gemm_fp64<<<grid_cap(ntiles, 1), NT, 0, st>>>(ntiles, jobs, njobs, cum_tiles, qb, w);
+  if (njobs == 0 || bound == 0) return;
+  switch (cfg) {
+    case 0: launch_shape<128, 128>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 1: launch_shape<128, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 2: launch_shape<64, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 3: launch_shape<64, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    default: launch_shape<32, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+  }
 }
 
 }  // namespace tdc

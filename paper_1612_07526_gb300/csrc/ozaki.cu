@@ -6,10 +6,11 @@
 //                 scale, then S bf16 digit slices written k-major;
 //   k_oz_slice_b  Qhat generated from (d, zhat, origin, tau, 1/norm) and split the
 //                 same way, one column of Qhat per k-major row;
-//   k_oz_gemm     128 x 64 output tiles: a TMA producer warp, an MMA warp and four
-//                 epilogue warps.  Seven to eight FP32 accumulators of 64 TMEM
-//                 columns (one per level p + q); exact levels are flushed every
-//                 256 k into 64-bit integers held by the epilogue threads.
+//   k_oz_gemm     128 x 64 output tiles: a TMA producer warp, an MMA warp and eight
+//                 epilogue warps.  Six to eight FP32 accumulators of 64 TMEM
+//                 columns (one per level p + q); one MMA per A slice and group of
+//                 up to four B slices; exact levels are flushed every 256 k into
+//                 64-bit integers held by the epilogue threads.
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
@@ -21,7 +22,8 @@ namespace tdc {
 
 namespace {
 
-constexpr int kThreads = 192;       // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr int kThreads = 320;       // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
+constexpr int kEpiWarps = 8;        // two per TMEM lane quadrant, each owning 32 of a level's 64 columns
 constexpr long long kWaitNs = 10LL * 1000 * 1000 * 1000;   // bounded mbarrier waits (10 s)
 
 __host__ __device__ constexpr int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -34,16 +36,50 @@ __device__ __forceinline__ int padded_to_grouped(int k, int c1, int c3, int K, i
   return r < K - c1 - c3 ? c1 + c3 + r : -1;
 }
 
-// Balanced base-256 digits of X (|X| <= 2^(8S-1)), most significant first, as bf16 bits.
+// Balanced base-256 digits of X (|X| <= 2^(8S-1)), most significant first, as bf16
+// bits.  With Y = X + sum_{p < S-1} 128 * 256^p, the S-1 low bytes of Y are d_p + 128
+// (d_p in [-128, 127] the balanced digits, least significant first) and the
+// arithmetic shift Y >> 8(S-1) is the top digit, in [-128, 128].  A byte b becomes
+// the float b - 128 by placing it in the mantissa of 2^23 and subtracting 2^23 + 128
+// (both exact); an integer of at most 8 significant bits is exact in bf16, whose bits
+// are the float's upper half.
 template <int S>
 __device__ __forceinline__ void digits_bf16(long long X, uint16_t (&out)[S]) {
+  unsigned long long bias = 0;
 #pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    const long long d = ((X + 128) & 255) - 128;
-    out[p] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
-    X = (X - d) >> 8;
+  for (int q = 0; q < S - 1; ++q) bias |= 128ull << (8 * q);
+  const unsigned long long Y = (unsigned long long)X + bias;
+  const uint32_t lo = (uint32_t)Y, hi = (uint32_t)(Y >> 32);
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) {
+    const uint32_t b = ((q < 4 ? lo >> (8 * q) : hi >> (8 * (q - 4)))) & 255u;
+    const float f = __uint_as_float(0x4B000000u | b) - 8388736.0f;
+    out[S - 1 - q] = (uint16_t)(__float_as_uint(f) >> 16);
   }
-  out[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)X));
+  const long long top = (long long)Y >> (8 * (S - 1));
+  out[0] = (uint16_t)(__float_as_uint((float)(int)top) >> 16);
+}
+
+// round(x * 2^k) to the nearest integer, ties to even, for |x 2^k| < 2^62, in
+// integer arithmetic on the bits of x (x = M 2^e2 with the integer significand M):
+// the scaled significand is shifted right with the discarded bits rounded.
+__device__ __forceinline__ long long round_scaled(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned long long F = b & 0xFFFFFFFFFFFFFull;
+  const unsigned long long M = E ? (F | (1ull << 52)) : F;
+  const int sh = -((E ? E - 1075 : -1074) + k);          // right shift of M
+  unsigned long long q;
+  if (sh <= 0) {
+    q = M << (-sh);
+  } else if (sh >= 64) {
+    q = 0;
+  } else {
+    q = M >> sh;
+    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
 }
 
 // ------------------------------------------------------------------------ PTX helpers
@@ -134,9 +170,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
-                            ((uint32_t)(kOzBM >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major,
+// M = 128 and N = 64 nq (nq stacked B slices).
+__host__ __device__ constexpr uint32_t idesc_n(int nq) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((kOzBN * nq) >> 3) << 17) |
+         ((uint32_t)(kOzBM >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 2^e for e in the normal range, built from its bit pattern (exact).
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
 struct JobView {
   int jb;
@@ -155,7 +204,7 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
                                                     const OzJob* __restrict__ ozj, int njobs,
                                                     const int64_t* __restrict__ cum, DevWs w) {
   __shared__ double tile[64][33];
-  __shared__ double s_max[8][32];
+  __shared__ unsigned long long s_max[8][32];
   __shared__ int s_exp[32];
   const JobView jv = job_of(cum, njobs);
   const MergeJob J = jobs[jv.jb];
@@ -175,17 +224,22 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
   const int tid = threadIdx.x;
   const int r = tid & 31, kq = tid >> 5;
   const bool rvalid = r0 + r < rows_h;
-  // pass 1: row maxima
-  double mx = 0.0;
+  // pass 1: row maxima, on the magnitude bits (integer order = order of |x|)
+  unsigned long long mx = 0ull;
   for (int k = kq; k < klen; k += 8) {
     const int kg = padded_to_grouped(kb + k, c1, c3, K, P1, P3);
-    if (kg >= 0 && rvalid) mx = fmax(mx, fabs(colptr[kg][rowbase + r0 + r]));
+    if (kg >= 0 && rvalid) {
+      const unsigned long long v =
+          (unsigned long long)__double_as_longlong(colptr[kg][rowbase + r0 + r]) & 0x7FFFFFFFFFFFFFFFull;
+      mx = v > mx ? v : mx;
+    }
   }
   s_max[kq][r] = mx;
   __syncthreads();
   if (tid < 32) {
-    double m = s_max[0][tid];
-    for (int q = 1; q < 8; ++q) m = fmax(m, s_max[q][tid]);
+    unsigned long long mb = s_max[0][tid];
+    for (int q = 1; q < 8; ++q) mb = s_max[q][tid] > mb ? s_max[q][tid] : mb;
+    const double m = __longlong_as_double((long long)mb);
     int e = 0;
     if (m > 0.0) frexp(m, &e);     // m < 2^e
     s_exp[tid] = e;
@@ -209,7 +263,7 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const double x = tile[wk + j][wr];
-        const long long X = __double2ll_rn(ldexp(x, shift));
+        const long long X = round_scaled(x, shift);
         uint16_t t[S];
         digits_bf16<S>(X, t);
 #pragma unroll
@@ -271,7 +325,7 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
       v = (zhat[jj] / ((dbar[jj] - dorg) - t)) * si;
     }
     uint16_t tt[S];
-    digits_bf16<S>(__double2ll_rn(ldexp(v, shift)), tt);
+    digits_bf16<S>(round_scaled(v, shift), tt);
 #pragma unroll
     for (int p = 0; p < S; ++p) dg[j][p] = tt[p];
   }
@@ -287,6 +341,12 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
 }
 
 // ------------------------------------------------------------------------ tcgen05 GEMM
+// MMA schedule.  Level L = p + q accumulates at TMEM columns (L - 2) * 64, so for a
+// fixed A slice p the products with the B slices q = qa .. qa + nq - 1 (stacked
+// contiguously in shared memory) land in the contiguous columns starting at
+// (p + qa - 2) * 64: one MMA of N = 64 nq covers them (nq <= 4, N <= 256).  Per 16-deep
+// k step that is 2S - 2 MMAs instead of one per pair, and each A slice is read from
+// shared memory once per group instead of once per pair.
 template <int S>
 struct OzCfg {
   static constexpr int NL = S + 1;                       // levels 2 .. S+2
@@ -296,6 +356,8 @@ struct OzCfg {
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int SMEM = ST * STAGE + 1024 + 256;
   static_assert(NL * kOzBN <= 512, "TMEM columns");
+  static_assert(S >= 4, "the chunk-reset MMA covers levels 2..5");
+  __host__ __device__ static constexpr int qmax(int p) { return S < S + 2 - p ? S : S + 2 - p; }
 };
 
 template <int S>
@@ -347,7 +409,7 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       mbar_init(empty(s), 1);
     }
     mbar_init(accfull, 1);
-    mbar_init(accempty, 4);
+    mbar_init(accempty, kEpiWarps);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -361,6 +423,17 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Every accumulator starts at zero, so that every MMA may accumulate; the exact
+  // levels are restarted at each chunk by the one MMA that covers all of them.
+  if (warp >= 2) {
+    const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(((warp - 2) >> 2) * 32);
+#pragma unroll
+    for (int L = 0; L < C::NL; ++L) tmem_st32_zero(tq + (uint32_t)(L * kOzBN));
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == 0) {
     if (lane == 0 && nst > 0) {
@@ -393,7 +466,6 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
     if (lane == 0 && nst > 0) {
       // ---------------- MMA issuer
       const int per_chunk = kOzChunk / kOzBK;
-      uint32_t started = 0;                 // tail accumulators already written
       for (int it = 0; it < nst; ++it) {
         const int s = it % C::ST;
         const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
@@ -407,33 +479,31 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
         bool ok = true;
 #pragma unroll
         for (int kk = 0; kk < kOzBK / 16; ++kk) {
-          // tail levels 6 .. S+2 (never reset after their first write)
+          // groups whose levels are all >= 6 (accumulated over the whole k range)
 #pragma unroll
-          for (int L = 6; L <= S + 2; ++L) {
+          for (int p = 1; p <= S; ++p) {
 #pragma unroll
-            for (int p = (L - S > 1 ? L - S : 1); p <= (S < L - 1 ? S : L - 1); ++p) {
-              const int q = L - p;
-              const uint32_t bit = 1u << L;
-              const uint32_t acc = (started & bit) ? 1u : 0u;
-              started |= bit;
-              tc_mma(tmem + (uint32_t)((L - 2) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
-                     sdesc(sb + (q - 1) * (kOzBN * kOzBK * 2) + kk * 32), kIdesc, acc);
+            for (int qa = 1; qa <= 5; qa += 4) {
+              if (qa <= C::qmax(p) && p + qa >= 6) {
+                const int nq = C::qmax(p) - qa + 1 < 4 ? C::qmax(p) - qa + 1 : 4;
+                tc_mma(tmem + (uint32_t)((p + qa - 2) * kOzBN),
+                       sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                       sdesc(sb + (qa - 1) * (kOzBN * kOzBK * 2) + kk * 32), idesc_n(nq), 1u);
+              }
             }
           }
           if (first && kk == 0 && chunk > 0) {
             if (!mbar_wait(accempty, (uint32_t)(chunk - 1) & 1u, abort_flag, err)) { ok = false; break; }
             tc_fence_after();
           }
-          // exact levels 2 .. 5, restarted at every chunk
+          // groups that touch the exact levels 2..5; (p = 1, q = 1..4) comes first and
+          // overwrites all four at the start of a chunk
 #pragma unroll
-          for (int L = 2; L <= 5; ++L) {
-#pragma unroll
-            for (int p = 1; p <= L - 1; ++p) {
-              const int q = L - p;
-              const uint32_t acc = (first && kk == 0 && p == 1) ? 0u : 1u;
-              tc_mma(tmem + (uint32_t)((L - 2) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
-                     sdesc(sb + (q - 1) * (kOzBN * kOzBK * 2) + kk * 32), kIdesc, acc);
-            }
+          for (int p = 1; p <= 4; ++p) {
+            const int nq = C::qmax(p) < 4 ? C::qmax(p) : 4;
+            const uint32_t acc = (p == 1 && first && kk == 0) ? 0u : 1u;
+            tc_mma(tmem + (uint32_t)((p - 1) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                   sdesc(sb + kk * 32), idesc_n(nq), acc);
           }
         }
         if (!ok) break;
@@ -444,15 +514,17 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       if (*abort_flag) mbar_wait(done, 0, abort_flag, err);
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4.
-    // Every tcgen05.ld below is executed by all 32 lanes (.sync.aligned); only the
-    // global stores are predicated on the row being inside the half.
+    // ---------------- epilogue: warps 2..9; TMEM lane quadrant = warp % 4, and the
+    // warp owns columns [32 half, 32 half + 32) of every level.  Every tcgen05.ld is
+    // executed by all 32 lanes (.sync.aligned); only the global stores are
+    // predicated on the row being inside the half.
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-    long long acc[64];
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 32);
+    long long acc[32];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    for (int j = 0; j < 32; ++j) acc[j] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const bool got = __all_sync(0xffffffffu, mbar_wait(accfull, (uint32_t)c & 1u, abort_flag, err));
@@ -460,15 +532,12 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       tc_fence_after();
 #pragma unroll
       for (int L = 2; L <= 5; ++L) {
+        uint32_t v[32];
+        tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t v[32];
-          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            acc[hh * 32 + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
-        }
+        for (int j = 0; j < 32; ++j)
+          acc[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
       }
       tc_fence_before();
       __syncwarp();
@@ -485,26 +554,32 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       double* out = J.src ? qb.A + J.off_a : qb.B + J.off_b;
       const int64_t ld = J.src ? J.lda : J.ldb;
       const int32_t* posK = w.posK + J.v_off;
+      // tail levels combined in FP32, smallest first: their rounding stays below the
+      // FP32 accumulation error that level 6 already carries
+      float tsum[32];
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        double dv[32];
+      for (int j = 0; j < 32; ++j) tsum[j] = 0.0f;
+      if (nst > 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dv[j] = ldexp((double)acc[hh * 32 + j], -38);
-        if (nst > 0) {
+        for (int L = S + 2; L >= 6; --L) {
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+          tmem_wait_ld();
+          const float wL = __int_as_float((127 - 8 * (L - 6)) << 23);     // 2^(-8 (L - 6))
 #pragma unroll
-          for (int L = 6; L <= S + 2; ++L) {
-            uint32_t v[32];
-            tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN + hh * 32), v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dv[j] += ldexp((double)__uint_as_float(v[j]), -(14 + 8 * (L - 2)));
-          }
+          for (int j = 0; j < 32; ++j) tsum[j] = fmaf(__uint_as_float(v[j]), wL, tsum[j]);
         }
-        if (rv) {
+      }
+      if (rv) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = ct * kOzBN + hh * 32 + j;
-            if (col < K) out[(int64_t)posK[col] * ld + rowbase + grow] = ldexp(dv[j] * sig, Z->texp[col]);
+        for (int j = 0; j < 32; ++j) {
+          const int col = ct * kOzBN + half * 32 + j;
+          if (col < K) {
+            // acc counts level-5 units (2^-38), tsum level-6 units (2^-46)
+            const double x = fma((double)tsum[j], 0x1p-8, (double)acc[j]);
+            const int e = Z->texp[col] - 38;
+            const double cs = e >= -1022 ? pow2(e) : ldexp(1.0, e);
+            out[(int64_t)posK[col] * ld + rowbase + grow] = (x * cs) * sig;
           }
         }
       }
@@ -519,19 +594,21 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
 }
 
 template <int S>
-void launch_s(const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa, int64_t nb_sa,
-              const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t, int64_t ntiles, QBufs qb,
-              DevWs w, int* err, cudaStream_t st) {
+void launch_s(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa, int64_t nb_sa,
+              const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t, int64_t ntiles, QBufs qb, DevWs w,
+              cudaStream_t st) {
   using C = OzCfg<S>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     attr = true;
   }
-  if (nb_sa) k_oz_slice_a<S><<<(unsigned)nb_sa, 256, 0, st>>>(jobs, ozj, njobs, cum_sa, w);
-  if (nb_sb) k_oz_slice_b<S><<<(unsigned)nb_sb, 256, 0, st>>>(jobs, ozj, njobs, cum_sb, w);
-  (void)err;
-  if (ntiles) k_oz_gemm<S><<<(unsigned)ntiles, kThreads, C::SMEM, st>>>(jobs, ozj, njobs, cum_t, qb, w);
+  if (part == 0) {
+    if (nb_sa) k_oz_slice_a<S><<<(unsigned)nb_sa, 256, 0, st>>>(jobs, ozj, njobs, cum_sa, w);
+    if (nb_sb) k_oz_slice_b<S><<<(unsigned)nb_sb, 256, 0, st>>>(jobs, ozj, njobs, cum_sb, w);
+  } else if (ntiles) {
+    k_oz_gemm<S><<<(unsigned)ntiles, kThreads, C::SMEM, st>>>(jobs, ozj, njobs, cum_t, qb, w);
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -604,14 +681,20 @@ int64_t oz_tiles(const MergeJob& J) {
   return ((J.n1 + kOzBM - 1) / kOzBM + (J.n2 + kOzBM - 1) / kOzBM) * ((m + kOzBN - 1) / kOzBN);
 }
 
-void launch_ozaki_level(const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
+void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
                         int64_t nb_sa, const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t,
-                        int64_t ntiles, int slices, QBufs qb, DevWs w, int* err, cudaStream_t st) {
+                        int64_t ntiles, int slices, QBufs qb, DevWs w, cudaStream_t st) {
   switch (slices) {
-    case 5: launch_s<5>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
-    case 7: launch_s<7>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
-    default: launch_s<6>(jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, err, st); break;
+    case 5: launch_s<5>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
+    case 7: launch_s<7>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
+    default: launch_s<6>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
   }
+}
+
+int oz_slice_pairs(int slices) {
+  int n = 0;
+  for (int p = 1; p <= slices; ++p) n += slices < slices + 2 - p ? slices : slices + 2 - p;
+  return n;
 }
 
 }  // namespace tdc

@@ -1,5 +1,8 @@
 // Product-path dispatch (see tdc_paths.cuh).
+#include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "tdc_hss.cuh"
 #include "tdc_ozaki.cuh"
@@ -11,7 +14,51 @@ namespace {
 __global__ void k_copy_k(const MergeScalars* scal, int64_t* k_out) { *k_out = scal[0].K; }
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, std::vector<int>> g_tune;
+LevelTimer* g_timer = nullptr;
+
+// Size rule: tile rows no larger than the merge halves, 32 columns for the smallest
+// merges, else 64 (K is known only on the device).
+int default_shape(int64_t maxm) {
+  if (maxm <= 64) return 4;
+  if (maxm <= 128) return 3;
+  return 1;
+}
 }  // namespace
+
+void path_set_shape(PathPlan& pp, int l, int cfg, const std::vector<MergeJob>& jobs) {
+  PathLevel& L = pp.levels[l];
+  L.gemm_cfg = cfg < 0 ? 0 : (cfg >= kGemmShapes ? kGemmShapes - 1 : cfg);
+  const int64_t bm = gemm_shape_rows(L.gemm_cfg), bn = gemm_shape_cols(L.gemm_cfg);
+  int64_t b = 0;
+  for (const MergeJob& J : jobs)
+    b += ((J.n1 + bm - 1) / bm + (J.n2 + bm - 1) / bm) * ((J.n1 + J.n2 + bn - 1) / bn);
+  L.gemm_bound = b;
+}
+
+std::vector<int64_t> tune_key(const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv) {
+  std::vector<int64_t> k{(int64_t)o.path, (int64_t)o.leaf, (int64_t)lv.size()};
+  for (const auto* jobs : lv) {
+    int64_t maxm = 0, sum = 0;
+    for (const MergeJob& J : *jobs) {
+      maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
+      sum += J.n1 + J.n2;
+    }
+    k.push_back((int64_t)jobs->size());
+    k.push_back(maxm);
+    k.push_back(sum);
+  }
+  return k;
+}
+
+void tune_store(const std::vector<int64_t>& key, const std::vector<int>& cfg) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[key] = cfg;
+}
+
+void set_level_timer(LevelTimer* t) { g_timer = t; }
 
 bool path_supported(const tdc_opts& o) {
   return o.path == TDC_PATH_DENSE_FP64 || o.path == TDC_PATH_DENSE_OZAKI || o.path == TDC_PATH_HSS ||
@@ -30,6 +77,13 @@ static int level_kind(const tdc_opts& o, int64_t maxm) {
 
 void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv) {
   pp.levels.assign(lv.size(), PathLevel{});
+  std::vector<int> tuned;
+  if (o.tile_cfg < 0) {
+    const std::vector<int64_t> key = tune_key(o, lv);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && it->second.size() == lv.size()) tuned = it->second;
+  }
   pp.slices = o.ozaki_slices < 5 ? 5 : (o.ozaki_slices > 7 ? 7 : o.ozaki_slices);
   pp.arena_bytes = 0;
   size_t tab = 0;
@@ -39,6 +93,8 @@ void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::
     for (const MergeJob& J : jobs) maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
     PathLevel& L = pp.levels[l];
     if (jobs.empty()) continue;
+    path_set_shape(pp, (int)l, o.tile_cfg >= 0 ? o.tile_cfg : (tuned.empty() ? default_shape(maxm) : tuned[l]),
+                   jobs);
     const int kind = level_kind(o, maxm);
     if (kind == 2) {
       L.hss = true;
@@ -95,10 +151,9 @@ bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
 }
 
 int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
-                   const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
-                   cudaStream_t st) {
-  phase_mark(5, true, 0, st);
+                   const MergeJob* jobs, int64_t* cum_tiles, QBufs qb, DevWs w, cudaStream_t st) {
   const PathLevel* L = (l >= 0 && l < (int)pp.levels.size()) ? &pp.levels[l] : nullptr;
+  if (!(L && L->oz)) phase_mark(5, true, 0, st);
   if (L && L->hss) {
     int rc = 0;
     for (const MergeJob& J : hjobs) {
@@ -113,12 +168,23 @@ int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vect
     const int64_t* c0 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[0]);
     const int64_t* c1 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[1]);
     const int64_t* c2 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[2]);
-    launch_ozaki_level(jobs, z, (int)hjobs.size(), c0, L->nb[0], c1, L->nb[1], c2, L->nb[2], pp.slices, qb,
-                       w, nullptr, st);
-    phase_mark(5, false, 3, st);
+    phase_mark(9, true, 0, st);
+    launch_ozaki_level(0, jobs, z, (int)hjobs.size(), c0, L->nb[0], c1, L->nb[1], c2, L->nb[2], pp.slices, qb,
+                       w, st);
+    phase_mark(9, false, 2, st);
+    phase_mark(8, true, 0, st);
+    launch_ozaki_level(1, jobs, z, (int)hjobs.size(), c0, L->nb[0], c1, L->nb[1], c2, L->nb[2], pp.slices, qb,
+                       w, st);
+    phase_mark(8, false, 1, st);
   } else {
-    launch_gemm_fp64(jobs, (int)hjobs.size(), cum_tiles, ntiles, qb, w, st);
-    phase_mark(5, false, 1, st);
+    const bool timed = g_timer && l >= 0 && l < (int)g_timer->a.size();
+    if (timed) cudaEventRecord(g_timer->a[l], st);
+    launch_gemm_fp64(L ? L->gemm_cfg : 1, jobs, (int)hjobs.size(), cum_tiles, L ? L->gemm_bound : 0, qb, w, st);
+    if (timed) {
+      cudaEventRecord(g_timer->b[l], st);
+      g_timer->used[l] = true;
+    }
+    phase_mark(5, false, 2, st);
   }
   return 0;
 }

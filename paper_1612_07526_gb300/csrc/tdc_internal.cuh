@@ -75,8 +75,13 @@ struct DevWs {
   double *rc, *rs;
   MergeScalars *scal;         // per merge id
   double *dmod;               // torn diagonal (Eq. 2 corner updates)
+  double2 *lrot;              // leaf QL: recorded plane rotations (c, s), kLeafRot per leaf
+  uint8_t *lroti;             // leaf QL: row index i of each rotation (rows i, i+1)
+  int32_t *lrotn;             // leaf QL: rotations recorded, or -1: redo the leaf serially
   int *status;                // per problem
 };
+
+constexpr int kLeafRot = 2048;   // rotations recorded per leaf (a 32-leaf needs about 1300)
 
 struct QBufs {
   double *A, *B, *S;          // ping-pong eigenvector buffers and the side buffer
@@ -119,18 +124,22 @@ unsigned grid_cap(int64_t nb, int per_sm);
 void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, int64_t ntear, int leaf,
                  const double* d, const double* e, double* dmod, int64_t ntot, cudaStream_t st);
 void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const double* e,
-                   double* lam, QBufs qb, int* status, cudaStream_t st);
+                   double* lam, QBufs qb, DevWs w, cudaStream_t st);
 void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                         const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
                         int max_iter, cudaStream_t st);
-void launch_gemm_fp64(const MergeJob* jobs, int njobs, const int64_t* cum_tiles, int64_t ntiles,
+// FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
+// 32x32.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
+// tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.
+void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_tiles, int64_t bound,
                       QBufs qb, DevWs w, cudaStream_t st);
+int gemm_shape_rows(int cfg);
+int gemm_shape_cols(int cfg);
 void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, int64_t nb_cols,
                       QBufs qb, DevWs w, bool any_root, cudaStream_t st);
 
 
-constexpr int kGemmBM = 128;
-constexpr int kGemmBN = 128;
+constexpr int kGemmShapes = 5;
 
 }  // namespace tdc

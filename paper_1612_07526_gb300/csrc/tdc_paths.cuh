@@ -13,6 +13,8 @@ namespace tdc {
 struct PathLevel {
   bool oz = false;
   bool hss = false;
+  int gemm_cfg = 1;          // FP64 product tile shape (levels on the FP64 product)
+  int64_t gemm_bound = 0;    // upper bound on its tiles (grid size)
   size_t tab_off = 0;        // OzJob array of the level in the table region
   size_t cum_off[3] = {0, 0, 0};
   int64_t nb[3] = {0, 0, 0}; // blocks: slice A, slice B, GEMM tiles
@@ -38,10 +40,23 @@ void path_prepare(PathPlan& pp, const tdc_opts& o, const std::vector<const std::
 // Binds the carved device regions, encodes the tensor maps and uploads the tables.
 bool path_bind(PathPlan& pp, unsigned char* arena, unsigned char* table_dev,
                const std::vector<const std::vector<MergeJob>*>& lv, cudaStream_t st);
-// Launches the product for all merges of level l.  Returns 0, or 3 / 4 from the HSS path.
+// Launches the product for all merges of level l.  cum_tiles is the level's device
+// scratch of njobs + 1 int64.  Returns 0, or 3 / 4 from the HSS path.
 int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vector<MergeJob>& hjobs,
-                    const MergeJob* jobs, const int64_t* cum_tiles, int64_t ntiles, QBufs qb, DevWs w,
-                    cudaStream_t st);
+                   const MergeJob* jobs, int64_t* cum_tiles, QBufs qb, DevWs w, cudaStream_t st);
+
+// FP64 product tile shapes per level.  The shape of a level is tile_cfg when that
+// is >= 0; otherwise the autotuned choice recorded for the same level structure
+// (tune_store), else a size rule (tile rows <= the merge halves, 32 or 64 columns).
+void path_set_shape(PathPlan& pp, int l, int cfg, const std::vector<MergeJob>& jobs);
+std::vector<int64_t> tune_key(const tdc_opts& o, const std::vector<const std::vector<MergeJob>*>& lv);
+void tune_store(const std::vector<int64_t>& key, const std::vector<int>& cfg);
+// While set, launch_product records an event pair around each FP64-product level.
+struct LevelTimer {
+  std::vector<cudaEvent_t> a, b;
+  std::vector<bool> used;
+};
+void set_level_timer(LevelTimer* t);
 void launch_copy_k(const MergeScalars* scal, int64_t* k_out, cudaStream_t st);
 
 }  // namespace tdc
