@@ -214,6 +214,21 @@ def context_measurements(api, _lib, lib, torch):
     return ctx
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (the job's time is the slowest replica's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_solve(step_ms_max, world):
+    """Replicas: each of `world` ranks solves one problem per step, so the job solves
+    `world` problems in the slowest rank's step time."""
+    return step_ms_max / 1000.0 / world
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -306,10 +321,7 @@ def main():
         lib.tdc_profile_end(ctypes.byref(prof))
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     bits = lib.tdc_read_status(api._vp(status), api._stream(stream))
 
     # accuracy of the last solve (sampled columns; the full checks live in the tests)
@@ -340,10 +352,8 @@ def main():
         for _ in range(args.steps):
             hs(dh, eh)
         t1 = time.perf_counter()
-        e_s = torch.tensor([(t1 - t0) / args.steps], device="cuda")
-        if dist is not None:
-            dist.all_reduce(e_s, op=dist.ReduceOp.MAX)
-        e2e = {"value": float(e_s.item()) / world, "unit": "s", "h2d_bytes_per_step": hs.h2d_bytes,
+        e_max = max_over_ranks((t1 - t0) / args.steps, dist, "cuda")
+        e2e = {"value": e_max / world, "unit": "s", "h2d_bytes_per_step": hs.h2d_bytes,
                "d2h_bytes_per_step": hs.d2h_bytes}
         del hs
         torch.cuda.empty_cache()
@@ -380,7 +390,7 @@ def main():
     if prof.defl_copy_bytes > 0 and prof.ms[6] > 0:
         cands.append({"bound": "hbm", "achieved": prof.defl_copy_bytes / (prof.ms[6] * 1e-3) / 1e9,
                       "peak": pk["hbm_gbs"], "unit": "GB/s", "ms_per_step": prof.ms[6] / args.steps,
-                      "kernel": "k_defl_copy: deflated columns to their sorted positions (16 B per entry)",
+                      "kernel": "k_defl_copy: deflated columns to their sorted positions (12 B per entry: live half read, column written)",
                       "peak_source": f"{pk_kind} HBM copy",
                       "algorithmic_per_step": prof.defl_copy_bytes / args.steps})
     for c in cands:
@@ -399,7 +409,7 @@ def main():
                          f"scaled by (n/{args.cpu_n})^3"}
 
     line = {
-        "metric": METRIC, "value": ms_max / 1000.0 / world, "unit": "s", "n_gpus": world,
+        "metric": METRIC, "value": job_seconds_per_solve(ms_max, world), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"tridiag eig+vecs n={n}, {args.gen} seed 0, leaf 32, path {args.path}",

@@ -56,7 +56,8 @@ typedef struct tdc_opts {
   int32_t ozaki_slices;      /* bf16 slices per operand (default 6, range 3..8)         */
   int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
   int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
-                             /* rule), 0..4 = 128x128, 128x64, 64x64, 64x32, 32x32     */
+                             /* rule), 0..5 = 128x128, 128x64, 64x64, 64x32, 32x32,    */
+                             /* 128x32                                                  */
   int32_t reserved;
 } tdc_opts;
 
@@ -178,7 +179,8 @@ typedef struct tdc_profile {
   double fp64_product_flops;       /* product_flops of the merges on the FP64 product */
   double split_product_flops;      /* product_flops of the merges on the split product */
   double split_tensor_flops;       /* bf16 tensor flops those run: slice pairs x 2 m K K */
-  double defl_copy_bytes;          /* 16 bytes x rows x deflated columns over merges   */
+  double defl_copy_bytes;          /* 12 bytes x rows x deflated columns over merges:
+                                      the live half read, the whole column written      */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);
@@ -225,7 +227,7 @@ int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, 
 void tdc_batched_plan_destroy(tdc_batched_plan* plan);
 
 /*
- * Autotuning of the FP64 product's tile shape per DC tree level (the five shapes of
+ * Autotuning of the FP64 product's tile shape per DC tree level (the six shapes of
  * tdc_opts.tile_cfg).  Every FP64 product sums each output element over k in the
  * same order whatever the shape, so the shape changes speed, never results.
  *

@@ -416,7 +416,7 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
         g_prof.fp64_flops += f;
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
-      g_prof.copy_bytes += 16.0 * m * (m - K);
+      g_prof.copy_bytes += 12.0 * m * (m - K);       // live half read, whole column written
       g_prof.merges += 1;
       g_prof.ktot += S.K;
     }

@@ -27,7 +27,7 @@ constexpr int BK = 8, NT = 256;
 struct Shape {
   int bm, bn;
 };
-constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32}, {32, 32}};
+constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32}, {32, 32}, {128, 32}};
 
 template <int BM, int BN>
 struct GemmSmem {
@@ -243,7 +243,8 @@ void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_til
     case 1: launch_shape<128, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 2: launch_shape<64, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 3: launch_shape<64, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
-    default: launch_shape<32, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 4: launch_shape<32, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    default: launch_shape<128, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
   }
 }
 

@@ -130,7 +130,7 @@ void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, 
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
                         int max_iter, cudaStream_t st);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
-// 32x32.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
+// 32x32, 128x32.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
 // tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.
 void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_tiles, int64_t bound,
                       QBufs qb, DevWs w, cudaStream_t st);
@@ -140,6 +140,6 @@ void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, 
                       QBufs qb, DevWs w, bool any_root, cudaStream_t st);
 
 
-constexpr int kGemmShapes = 5;
+constexpr int kGemmShapes = 6;
 
 }  // namespace tdc
