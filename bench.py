@@ -147,7 +147,35 @@ def cpu_oracle_sample(gen, n_full, n_s):
     return t * (n_full / n_s) ** 3, t, cores
 
 
-def profiled_solve(api, _lib, lib, torch, d, e, path, **kw):
+def sampled_accuracy(torch, d, e, lam, q, ncol=32, seed=1):
+    """Orthogonality of `ncol` sampled eigenvectors against all of them (max |Q^T q_s - e_s|)
+    and their scaled residual ||T q - lambda q||_F / (sqrt(ncol/n) n eps ||T||_1),
+    eps = 2^-52, computed with torch on the GPU from the definitions."""
+    import numpy as np
+    n = len(d)
+    ncol = min(ncol, n)
+    sel = np.random.Generator(np.random.PCG64(seed)).choice(n, ncol, replace=False)
+    idx = torch.tensor(sel, device=q.device)
+    qs = q[:, idx]
+    gram = q.t() @ qs
+    gram[idx, torch.arange(ncol, device=q.device)] -= 1.0
+    dt = torch.tensor(d, device=q.device)
+    et = torch.tensor(e, device=q.device)
+    tq = dt[:, None] * qs
+    if n > 1:
+        tq[:-1] += et[:, None] * qs[1:]
+        tq[1:] += et[:, None] * qs[:-1]
+    r = tq - qs * lam[idx][None, :]
+    row = dt.abs().clone()
+    if n > 1:
+        row[:-1] += et.abs()
+        row[1:] += et.abs()
+    tnorm = float(row.max())
+    return {"orth_max_sampled": float(gram.abs().max()),
+            "resid_scaled_sampled": float(torch.linalg.norm(r)) / (ncol / n) ** 0.5 / (n * 2.0 ** -52 * tnorm)}
+
+
+def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
     """One warm-up and one timed solve with per-phase events; returns a summary."""
     import ctypes
     n = len(d)
@@ -173,28 +201,70 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, **kw):
         out["split_gemm_ms"] = p.ms[8]
         out["split_operand_split_ms"] = p.ms[9]
         out["split_gemm_bf16_tflops"] = p.split_tensor_flops / (p.ms[8] * 1e-3) / 1e12
+    out["phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES)}
+    out["K_total"] = int(p.K_total)
+    out["accuracy"] = sampled_accuracy(torch, d, e, lam, q)
+    if exact is not None:           # closed-form eigenvalues: max |error| / (n eps ||T||)
+        lh = lam.cpu().numpy()
+        tn = float(max(abs(d).max() + 2 * abs(e).max(), 1e-300))
+        out["accuracy"]["eig_err_scaled_closed_form"] = float(abs(lh - exact).max()) / (n * 2.0 ** -52 * tn)
     del q
     torch.cuda.empty_cache()
     return out
 
 
 def context_measurements(api, _lib, lib, torch):
-    """Few-deflation solves (tridiag(1,2,1), the paper's Example 2/3 matrix) with each
-    product form, and the batched configuration (ragged problems, graph replay)."""
+    """Context runs beside the headline:
+    - the few-deflation case tridiag(1,2,1) (Examples 2-3) with each product form;
+    - the headline matrix and the graded matrix of the same configuration on the split
+      product, with their accuracy (error per result);
+    - the paper's example matrices at n = 30000 (Clement, Hermite, tridiag(1,2,1), SHT of
+      Example 4) on the split product, with per-phase times (a Table 2 analog) and the
+      closed-form eigenvalues where there are any;
+    - a sweep of the AUTO path's K threshold (HSS above it, split product below);
+    - the batched configuration (ragged problems, autotuned tiles, graph replay)."""
     import numpy as np
     import workloads as W
     ctx = {}
     d, e = W.toeplitz_121(32768)
-    ctx["toeplitz_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
+    k = np.arange(1, 32769)
+    ctx["toeplitz_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki",
+                                                 exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
+    ctx["toeplitz_32768_split_7slices"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", ozaki_slices=7,
+                                                         exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
+    d, e = W.uniform_tridiag(32768, 0)
+    ctx["uniform_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
+    d, e = W.graded_tridiag(32768, 0)
+    ctx["graded_32768_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64")
+    ctx["graded_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
     d, e = W.toeplitz_121(16384)
-    ctx["toeplitz_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64")
-    ctx["toeplitz_16384_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
-    ctx["toeplitz_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss")
+    k = np.arange(1, 16385)
+    ex = 2.0 - 2.0 * np.cos(k * np.pi / 16385)
+    ctx["toeplitz_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64", exact=ex)
+    ctx["toeplitz_16384_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", exact=ex)
+    ctx["toeplitz_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss", exact=ex)
+    d, e = W.normal_tridiag(16384, 0)
+    ctx["normal_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64")
+    ctx["normal_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss")
+    n = 30000
+    ex_clement = np.arange(-(n - 1), n, 2, dtype=np.float64)
+    for name, (d, e), ex in (("clement", W.clement(n), ex_clement),
+                             ("hermite", W.hermite(n), None),
+                             ("toeplitz", W.toeplitz_121(n), 2.0 - 2.0 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))),
+                             ("sht", W.sht(n), None)):
+        ctx[f"paper_{name}_30000_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", exact=ex)
+    d, e = W.toeplitz_121(16384)
+    sweep = {}
+    for kt in (2048, 4096, 8192, 16385):
+        r = profiled_solve(api, _lib, lib, torch, d, e, "auto", k_threshold=kt)
+        sweep[str(kt)] = {"ms": r["ms"], "accuracy": r["accuracy"]}
+    ctx["auto_k_threshold_sweep_toeplitz_16384"] = sweep
     # batched: 4096 problems, n log-uniform in [32, 2048], d, e ~ N(0, 1)
     sizes, probs = W.batched_normal(4096, seed=0)
     plan = api.BatchedPlan(sizes, opts={"path": PATHS["fp64"]})
     d_cat, e_cat = plan.pack([p[0] for p in probs], [p[1] for p in probs])
     lam, q = plan.outputs()
+    shapes = plan.autotune(d_cat, e_cat, lam, q)
     plan.capture(d_cat, e_cat, lam, q)
     for _ in range(2):
         plan.replay()
@@ -208,7 +278,8 @@ def context_measurements(api, _lib, lib, torch):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
     ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
-                           "status_nonzero": int((plan.status != 0).sum())}
+                           "status_nonzero": int((plan.status != 0).sum()),
+                           "tile_shapes": ",".join(map(str, shapes))}
     del plan, q, lam
     torch.cuda.empty_cache()
     return ctx
@@ -327,18 +398,8 @@ def main():
     # accuracy of the last solve (sampled columns; the full checks live in the tests)
     acc = {}
     if rank == 0:
-        from oracle import metrics
-        gsel = np.random.Generator(np.random.PCG64(1)).choice(n, 32, replace=False)
-        qs = q[:, torch.tensor(gsel, device="cuda")]
-        gram = (q.t() @ qs).cpu().numpy()
-        gram[gsel, np.arange(32)] -= 1.0
-        qs = qs.cpu().numpy()
-        lh = lam.cpu().numpy()
-        r = metrics.tri_matmul(d, e, qs) - qs * lh[gsel][None, :]
-        nrm = metrics.tnorm(d, e)
-        acc = {"orth_max_sampled": float(np.abs(gram).max()),
-               "resid_scaled_sampled": float(np.linalg.norm(r) / np.sqrt(32 / n) / (n * 2.0 ** -52 * nrm)),
-               "status": int(bits)}
+        acc = sampled_accuracy(torch, d, e, lam, q)
+        acc["status"] = int(bits)
 
     # end to end through the host-memory entry point (pinned buffers)
     e2e = None

@@ -53,7 +53,8 @@ typedef struct tdc_opts {
   int32_t hss_leaf;          /* HSS leaf block size (default 512)                       */
   int32_t hss_rp;            /* random samples r + p (default 128)                      */
   int64_t k_threshold;       /* AUTO: HSS only for merges with K >= this (default 8192) */
-  int32_t ozaki_slices;      /* bf16 slices per operand (default 6, range 3..8)         */
+  int32_t ozaki_slices;      /* bf16 slices per operand (default 6, range 5..7; 7 gives */
+                             /* FP64-level accuracy for 34 instead of 26 slice products)  */
   int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
   int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
                              /* rule), 0..5 = 128x128, 128x64, 64x64, 64x32, 32x32,    */

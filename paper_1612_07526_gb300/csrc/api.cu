@@ -232,7 +232,7 @@ static tdc_opts resolve_opts(const tdc_opts* o) {
 
 static bool opts_valid(const tdc_opts& o) {
   return o.path >= TDC_PATH_DENSE_FP64 && o.path <= TDC_PATH_AUTO && o.leaf >= 1 && o.leaf <= 32 &&
-         o.max_secular_iter >= 1 && o.ozaki_slices >= 3 && o.ozaki_slices <= 8 && o.hss_leaf >= 16 &&
+         o.max_secular_iter >= 1 && o.ozaki_slices >= 5 && o.ozaki_slices <= 7 && o.hss_leaf >= 16 &&
          o.hss_rp >= 8 && o.hss_tol > 0.0;
 }
 

@@ -91,3 +91,31 @@ def test_full_size_toeplitz_16384_ozaki(api):
     qs = qs.cpu().numpy()
     r = metrics.tri_matmul(d, e, qs) - qs * lam[cols][None, :]
     assert np.linalg.norm(r) / np.sqrt(64 / n) <= 10 * n * EPS * 4.0
+
+
+@pytest.mark.parametrize("slices,tol", [(5, 1e-11), (6, 2e-14), (7, 3e-15)])
+def test_merge_slice_counts(api, slices, tol):
+    """S digit slices represent each scaled entry to 2^-8S, so the product's distance
+    to the FP64 product shrinks by about 2^8 per slice (S = 7 is at FP64 rounding)."""
+    n1, n2 = 1024, 1000
+    D, Q, beta = W.merge_problem(n1, n2, 5)
+    n = n1 + n2
+    lam_o, q_o, K_o = api.merge(torch.tensor(D, device="cuda"), _fortran(Q), n1, beta,
+                                opts={"path": OZ, "ozaki_slices": slices})
+    lam_f, q_f, K_f = api.merge(torch.tensor(D, device="cuda"), _fortran(Q), n1, beta, opts={"path": 0})
+    assert K_o == K_f and torch.equal(lam_o, lam_f)
+    q_o = q_o.cpu().numpy()
+    assert np.max(np.abs(q_o - q_f.cpu().numpy())) <= tol
+    assert np.max(np.abs(q_o.T @ q_o - np.eye(n))) <= 100 * n * EPS
+
+
+def test_syev_seven_slices_accuracy(api):
+    n = 4096
+    d, e = W.toeplitz_121(n)
+    lam_t, q_t = api.syev_tridiag(torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda"),
+                                  opts={"path": OZ, "ozaki_slices": 7})
+    lam, q = lam_t.cpu().numpy(), q_t.cpu().numpy()
+    lref, _ = sturm.closed_form_121(n)
+    assert np.max(np.abs(lam - lref)) <= 10 * n * EPS * 4.0
+    assert metrics.scaled_residual(d, e, lam, q) <= 1.0     # S = 6 gives about 4 here
+    assert metrics.orthogonality(q) <= 100 * n * EPS
