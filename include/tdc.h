@@ -205,7 +205,7 @@ int tdc_profile_end(tdc_profile* out);
  *   Returns -1 if n < 1 or n > TDC_NOALLOC_MAX_N, otherwise as tdc_syev_tridiag.
  */
 #define TDC_NOALLOC_MAX_N 512
-#define TDC_NOALLOC_SCRATCH_BYTES (6u << 20)
+#define TDC_NOALLOC_SCRATCH_BYTES (8u << 20)
 int tdc_syev_tridiag_noalloc(int64_t n, const double* d, const double* e, double* lambda,
                              double* Q, int64_t ldq, int* dev_status, void* stream);
 

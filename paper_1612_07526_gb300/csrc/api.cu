@@ -20,11 +20,8 @@ namespace tdc {
 struct ProblemDesc {
   int64_t n;
   int64_t vbase;            // vector offset
-  int64_t qa, lda;          // buffer A: offset of (0,0), leading dimension
-  int64_t qb, ldb;          // buffer B
-  int64_t qs, lds;          // side buffer
-  int64_t e_base;           // e index of the first off-diagonal, or -1 (single merge)
-  double beta;              // single merge only
+  int64_t qa, lda;          // the caller's output: offset of (0,0), leading dimension
+  int64_t pool;             // offset of the problem's pool (3n columns of n rows) in the pools
 };
 
 struct LevelPlan {
@@ -49,12 +46,13 @@ static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int6
   if (n <= leaf) {
     LeafJob L{};
     L.v_off = pd.vbase + lo;
-    L.buf = (depth % 2 == 0) ? 0 : 1;
-    L.q_off = L.buf ? pd.qb + lo * pd.ldb + lo : pd.qa + lo * pd.lda + lo;
-    L.ld = (int32_t)(L.buf ? pd.ldb : pd.lda);
+    L.buf = depth == 0 ? 0 : 1;                 // a whole problem writes the caller's array
+    L.q_off = L.buf ? pd.pool + lo * pd.n + lo : pd.qa + lo * pd.lda + lo;
+    L.ld = (int32_t)(L.buf ? pd.n : pd.lda);
     L.nl = (int32_t)n;
     L.prob = prob;
     L.root = depth == 0 ? 1 : 0;
+    L.lo = (int32_t)lo;
     P.leaves.push_back(L);
     return 0;
   }
@@ -65,20 +63,20 @@ static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int6
   const int h = std::max(h1, h2) + 1;
   MergeJob J{};
   J.v_off = pd.vbase + lo;
-  J.off_a = pd.qa + lo * pd.lda + lo;
-  J.off_b = pd.qb + lo * pd.ldb + lo;
-  J.off_s = pd.qs + lo * pd.lds + lo;
-  J.lda = pd.lda;
-  J.ldb = pd.ldb;
-  J.lds = pd.lds;
+  J.out_off = pd.qa + lo * pd.lda + lo;
+  J.ld_out = pd.lda;
+  J.pool_off = pd.pool;
+  J.pn = (int32_t)pd.n;
+  J.lo = (int32_t)lo;
   J.n1 = (int32_t)n1;
   J.n2 = (int32_t)(n - n1);
-  J.src = ((depth + 1) % 2 == 0) ? 0 : 1;
   J.prob = prob;
+  J.fin = depth == 0 ? 1 : 0;
   J.e_idx = pd.vbase + lo + n1 - 1;
   J.beta = 0.0;
   J.mid = P.nmerges++;
   J.root = depth == 0 ? 1 : 0;
+  J.ext = 0;
   if ((int)P.levels.size() < h) P.levels.resize(h);
   P.levels[h - 1].jobs.push_back(J);
   P.maxm = std::max(P.maxm, n);
@@ -161,8 +159,7 @@ struct Carver {
 
 struct Layout {
   DevWs w{};
-  double* qb = nullptr;       // buffer B (ping-pong partner)
-  double* qs = nullptr;       // side buffer
+  double* pool = nullptr;     // the problems' pools: 3 n x n per problem
   unsigned char* plan = nullptr;
   unsigned char* arena = nullptr;
   unsigned char* table = nullptr;
@@ -174,8 +171,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   Carver c{reinterpret_cast<unsigned char*>(ws)};
   Layout L;
   const size_t N = (size_t)std::max<int64_t>(nvec, 1);
-  L.qb = c.take<double>((size_t)qwords);
-  L.qs = c.take<double>((size_t)qwords);
+  L.pool = c.take<double>(3 * (size_t)qwords);
   DevWs& w = L.w;
   w.ds = c.take<double>(N);
   w.zs = c.take<double>(N);
@@ -210,6 +206,14 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.sval = c.take<int32_t>(2 * N);
   w.colptr = c.take<const double*>(N);
   w.dcolptr = c.take<const double*>(N);
+  w.klo = c.take<int32_t>(N);
+  w.khi = c.take<int32_t>(N);
+  w.dlo = c.take<int32_t>(N);
+  w.dhi = c.take<int32_t>(N);
+  w.outptr = c.take<double*>(N);
+  w.tptr = c.take<const double*>(N);
+  w.tlo = c.take<int32_t>(N);
+  w.thi = c.take<int32_t>(N);
   w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
   const size_t NL = (size_t)std::max<int64_t>(nleaf, 1);
   w.lrot = c.take<double2>(NL * kLeafRot);
@@ -270,9 +274,14 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
                        o.max_secular_iter, st);
     const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
     if (prc) return prc;
-    bool any_root = false;
-    for (const MergeJob& J : lv.jobs) any_root |= J.root != 0;
-    launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, sign_norm && any_root, st);
+    bool any_root = false, any_fin = false;
+    for (const MergeJob& J : lv.jobs) {
+      any_root |= J.root != 0;
+      any_fin |= J.fin != 0;
+    }
+    // deflated columns move only in a problem's top merge; below, the slot table keeps them in place
+    if (any_fin)
+      launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, sign_norm && any_root, st);
   }
   (void)qa_for_sign;
   return 0;
@@ -416,7 +425,7 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
         g_prof.fp64_flops += f;
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
-      g_prof.copy_bytes += 12.0 * m * (m - K);       // live half read, whole column written
+      if (J.fin) g_prof.copy_bytes += 12.0 * m * (m - K);   // live half read, whole column written
       g_prof.merges += 1;
       g_prof.ktot += S.K;
     }
@@ -436,10 +445,7 @@ static void single_problem_plan(Plan& P, int64_t n, int64_t ldq, int leaf) {
   pd.vbase = 0;
   pd.qa = 0;
   pd.lda = ldq;
-  pd.qb = 0;
-  pd.ldb = n;
-  pd.qs = 0;
-  pd.lds = n;
+  pd.pool = 0;
   build_plan(P, {pd}, leaf);
 }
 
@@ -474,7 +480,7 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   cudaMemsetAsync(L.w.status, 0, sizeof(int), st);
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
-  QBufs qb{Q, L.qb, L.qs};
+  QBufs qb{Q, L.pool, nullptr};
   const int prc = run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
   if (prc) return prc;
   if (profile_accounting) prof_account(P, pp, L.w.scal, st);
@@ -543,7 +549,7 @@ int tdc_autotune(int64_t n, const double* d, const double* e, double* lambda, do
   if (dev_status) L.w.status = dev_status;
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
-  QBufs qb{Q, L.qb, L.qs};
+  QBufs qb{Q, L.pool, nullptr};
   std::vector<int> best;
   const int rc = autotune_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, st, best);
   if (rc) return rc;
@@ -633,15 +639,18 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   P.levels.resize(1);
   MergeJob J{};
   J.v_off = 0;
-  J.off_a = 0;
-  J.lda = ldq;
-  J.off_b = 0;
-  J.ldb = ldqo;
-  J.off_s = 0;
-  J.lds = n;
+  J.out_off = 0;
+  J.ld_out = ldqo;
+  J.pool_off = 0;
+  J.pn = (int32_t)n;
+  J.lo = 0;
+  J.in_off = 0;
+  J.ld_in = ldq;
+  J.ext = 1;                     // inputs: the caller's Q
+  J.fin = 1;                     // outputs: the caller's Q_out in sorted order, no sign convention
+  J.root = 0;
   J.n1 = (int32_t)n1;
   J.n2 = (int32_t)n2;
-  J.src = 0;
   J.prob = 0;
   J.beta = beta;
   J.e_idx = -1;
@@ -661,7 +670,7 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   cudaMemcpyAsync(lambda, D, n * 8, cudaMemcpyDeviceToDevice, st);
-  QBufs qb{const_cast<double*>(Q), Q_out, L.qs};
+  QBufs qb{Q_out, L.pool, Q};
   const LevelPlan& lv = P.levels[0];
   const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
   launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
@@ -683,7 +692,7 @@ size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const t
   for (int p = 0; p < batch; ++p) {
     const int64_t n = n_host[p];
     if (n < 1) return 0;
-    probs[p] = ProblemDesc{n, vtot, qtot, n, qtot, n, qtot, n, -1, 0.0};
+    probs[p] = ProblemDesc{n, vtot, qtot, n, 3 * qtot};
     vtot += n;
     qtot += n * n;
     maxn = std::max(maxn, n);
@@ -723,7 +732,7 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
     if (n < 1) return -2;
     if (off_de[p] != vtot) return -3;
     if (off_q[p] < 0) return -4;
-    probs[p] = ProblemDesc{n, vtot, off_q[p], n, qtot, n, qtot, n, -1, 0.0};
+    probs[p] = ProblemDesc{n, vtot, off_q[p], n, 3 * qtot};
     vtot += n;
     qtot += n * n;
     maxn = std::max(maxn, n);
@@ -739,7 +748,7 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
   cudaMemsetAsync(L.w.status, 0, sizeof(int) * batch, st);
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
-  QBufs qb{Q_cat, L.qb, L.qs};
+  QBufs qb{Q_cat, L.pool, nullptr};
   const int prc = run_plan(P, pp, L, o, d_cat, e_cat, lambda_cat, qb, vtot, batch, true, Q_cat, st);
   if (prc) return prc;
   prof_account(P, pp, L.w.scal, st);
@@ -810,7 +819,7 @@ int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts
       delete h;
       return -2;
     }
-    probs[p] = ProblemDesc{n, vtot, qtot, n, qtot, n, qtot, n, -1, 0.0};
+    probs[p] = ProblemDesc{n, vtot, qtot, n, 3 * qtot};
     vtot += n;
     qtot += n * n;
   }
@@ -847,7 +856,7 @@ int tdc_batched_plan_execute(const tdc_batched_plan* h, const double* d_cat, con
   Layout L = h->L;
   if (dev_status_per_problem) L.w.status = dev_status_per_problem;
   cudaMemsetAsync(L.w.status, 0, sizeof(int) * h->batch, st);
-  QBufs qb{Q_cat, L.qb, L.qs};
+  QBufs qb{Q_cat, L.pool, nullptr};
   const int prc = run_plan(h->P, h->pp, L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, true, Q_cat, st);
   if (prc) return prc;
   return launch_status();
@@ -863,7 +872,7 @@ int tdc_batched_plan_autotune(tdc_batched_plan* h, const double* d_cat, const do
   if (!Q_cat) return -5;
   if (shape_per_level && max_levels < 0) return -7;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  QBufs qb{Q_cat, h->L.qb, h->L.qs};
+  QBufs qb{Q_cat, h->L.pool, nullptr};
   std::vector<int> best;
   const int rc = autotune_plan(h->P, h->pp, h->L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, st, best);
   if (rc) return rc;

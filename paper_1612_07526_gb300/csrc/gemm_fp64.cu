@@ -88,9 +88,13 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   auto load_a = [&](int k0) {
     const int k = k0 + la_k;
     if (k < kend) {
-      const double* col = colptr[k] + r0;
+      const double* col = colptr[k];
+      const int lo = max(w.klo[o + k], r0), hi = min(w.khi[o + k], rend);   // rows that can be nonzero
 #pragma unroll
-      for (int u = 0; u < LA; ++u) ra[u] = (r0 + la_r + u < rend) ? col[la_r + u] : 0.0;
+      for (int u = 0; u < LA; ++u) {
+        const int r = r0 + la_r + u;
+        ra[u] = (r >= lo && r < hi) ? col[r] : 0.0;
+      }
     } else {
 #pragma unroll
       for (int u = 0; u < LA; ++u) ra[u] = 0.0;
@@ -155,14 +159,11 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
     }
   }
 
-  double* out = (J.src ? qb.A + J.off_a : qb.B + J.off_b);
-  const int64_t ld = J.src ? J.lda : J.ldb;
 #pragma unroll
   for (int b = 0; b < TN; ++b) {
     const int c = ty + 16 * b;
-    const int pos = sm.pos[c];
-    if (pos < 0) continue;
-    double* col = out + (int64_t)pos * ld + r0;
+    if (sm.pos[c] < 0) continue;
+    double* col = w.outptr[o + ct * BN + c] + r0;
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
       const int r = tx + 16 * a;

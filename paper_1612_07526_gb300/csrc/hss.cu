@@ -57,9 +57,7 @@ __device__ __forceinline__ double fetch(const HOp& op, const QhatSrc& q, const H
     }
     case HOP_XCOLS: {
       const int j = op.c0 + c;                 // kept (sorted-d) column index
-      const int t = xc.type[j];
-      const bool live = r < xc.n1 ? (t & 1) : (t & 2);
-      return live ? xc.col[j][r] : 0.0;
+      return r >= xc.lo[j] && r < xc.hi[j] ? xc.col[j][r] : 0.0;
     }
     case HOP_STACK: {                          // columns [0, k1) from p, the rest from p2
       const int k1 = *op.split;
@@ -124,6 +122,7 @@ __global__ __launch_bounds__(256) void k_hss_gemm(const HGemm* __restrict__ jobs
     if (c >= N) continue;
     double* col;
     if (G.cmode == HC_SCATTER) col = G.C + (int64_t)G.cpos[G.cc0 + c] * G.ldc;
+    else if (G.cmode == HC_PTRS) col = G.cptrs[G.cc0 + c];
     else col = G.C + (int64_t)c * G.ldc;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -160,7 +159,8 @@ __global__ void k_hss_cols(const MergeJob J, DevWs w, HssCols xc) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     const int j = w.kperm[o + k];
     xc.col[j] = w.colptr[o + k];
-    xc.type[j] = w.typ[o + w.kidx[o + j]];
+    xc.lo[j] = w.klo[o + k];
+    xc.hi[j] = w.khi[o + k];
   }
 }
 
@@ -465,7 +465,8 @@ void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts&
   L.Y = b.take<double>((size_t)K * rp);
   L.Z = b.take<double>((size_t)K * rp);
   L.xc.col = b.take<const double*>(K);
-  L.xc.type = b.take<int32_t>(K);
+  L.xc.lo = b.take<int32_t>(K);
+  L.xc.hi = b.take<int32_t>(K);
   L.tree.clear();
   L.root = build_tree(L.tree, 0, std::max(K, 1), 0, hl);
   const int nn = (int)L.tree.size();
@@ -575,8 +576,7 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   QhatSrc q{w.dbar + o_v, w.zhat + o_v, w.org + o_v, w.tau + o_v, w.sinv + o_v};
   HssCols xc = L.xc;
   xc.n1 = hJ.n1;
-  double* outbuf = hJ.src ? qb.A + hJ.off_a : qb.B + hJ.off_b;
-  const int64_t ldo = hJ.src ? hJ.lda : hJ.ldb;
+  double* const* outp = w.outptr + o_v;     // output column of each kept eigenpair
   cudaMemcpyAsync(L.dnodes, nd.data(), nn * sizeof(HssNodeDev), cudaMemcpyHostToDevice, st);
   size_t toff = 0;
   unsigned char* tab = L.tab;
@@ -732,14 +732,14 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       a.M = m; a.N = sz; a.K = sz;
       a.a.mode = HOP_XCOLS; a.a.c0 = lo;
       a.b.mode = HOP_QHAT; a.b.r0 = lo; a.b.c0 = lo;
-      a.cmode = HC_SCATTER; a.C = outbuf; a.ldc = ldo; a.cpos = w.posK + o_v; a.cc0 = lo;
+      a.cmode = HC_PTRS; a.cptrs = outp; a.cc0 = lo;
       g1.push_back(a);
       if (nn > 1) {
         HGemm b = gemm0();
         b.M = m; b.N = sz; b.K = rp; b.Kdev = nd[i].kV;
         b.a.mode = HOP_DENSE; b.a.p = nd[i].F; b.a.ld = m;
         b.b.mode = HOP_DENSE_T; b.b.p = nd[i].V; b.b.ld = rmax;
-        b.cmode = HC_SCATTER; b.C = outbuf; b.ldc = ldo; b.cpos = w.posK + o_v; b.cc0 = lo;
+        b.cmode = HC_PTRS; b.cptrs = outp; b.cc0 = lo;
         b.beta = 1.0;
         g2.push_back(b);
       }

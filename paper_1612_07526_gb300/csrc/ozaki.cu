@@ -228,9 +228,10 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
   unsigned long long mx = 0ull;
   for (int k = kq; k < klen; k += 8) {
     const int kg = padded_to_grouped(kb + k, c1, c3, K, P1, P3);
-    if (kg >= 0 && rvalid) {
+    const int row = rowbase + r0 + r;
+    if (kg >= 0 && rvalid && row >= w.klo[J.v_off + kg] && row < w.khi[J.v_off + kg]) {
       const unsigned long long v =
-          (unsigned long long)__double_as_longlong(colptr[kg][rowbase + r0 + r]) & 0x7FFFFFFFFFFFFFFFull;
+          (unsigned long long)__double_as_longlong(colptr[kg][row]) & 0x7FFFFFFFFFFFFFFFull;
       mx = v > mx ? v : mx;
     }
   }
@@ -255,7 +256,9 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
     for (int kk = 0; kk < 8; ++kk) {
       const int k = kq * 8 + kk;
       const int kg = padded_to_grouped(kb + k0 + k, c1, c3, K, P1, P3);
-      tile[k][r] = (kg >= 0 && rvalid && k0 + k < klen) ? colptr[kg][rowbase + r0 + r] : 0.0;
+      const int row = rowbase + r0 + r;
+      tile[k][r] = (kg >= 0 && rvalid && k0 + k < klen && row >= w.klo[J.v_off + kg] &&
+                    row < w.khi[J.v_off + kg]) ? colptr[kg][row] : 0.0;
     }
     __syncthreads();
     if (r0 + wr < rows_h) {
@@ -551,9 +554,7 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
     const bool rv = grow < rows_h;
     if (ok) {
       const double sig = rv ? Z->sigma[rowbase + grow] : 0.0;
-      double* out = J.src ? qb.A + J.off_a : qb.B + J.off_b;
-      const int64_t ld = J.src ? J.lda : J.ldb;
-      const int32_t* posK = w.posK + J.v_off;
+      double* const* outptr = w.outptr + J.v_off;
       // tail levels combined in FP32, smallest first: their rounding stays below the
       // FP32 accumulation error that level 6 already carries
       float tsum[32];
@@ -579,7 +580,7 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
             const double x = fma((double)tsum[j], 0x1p-8, (double)acc[j]);
             const int e = Z->texp[col] - 38;
             const double cs = e >= -1022 ? pow2(e) : ldexp(1.0, e);
-            out[(int64_t)posK[col] * ld + rowbase + grow] = (x * cs) * sig;
+            outptr[col][rowbase + grow] = (x * cs) * sig;
           }
         }
       }

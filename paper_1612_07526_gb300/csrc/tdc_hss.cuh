@@ -10,7 +10,7 @@ namespace tdc {
 
 enum : int { HOP_DENSE = 0, HOP_DENSE_T = 1, HOP_QHAT = 2, HOP_QHAT_T = 3, HOP_XCOLS = 4, HOP_STACK = 5,
              HOP_STACK_ROWS = 6 };
-enum : int { HC_DENSE = 0, HC_SCATTER = 1 };
+enum : int { HC_DENSE = 0, HC_SCATTER = 1, HC_PTRS = 2 };
 
 // One operand of a batched GEMM, as a logical matrix element (r, c).
 struct HOp {
@@ -36,13 +36,14 @@ struct HGemm {
   double* C;
   int64_t ldc;
   const int32_t* cpos;        // scatter: output column of logical column c is cpos[cc0 + c]
+  double* const* cptrs;       // pointers: output column of logical column c is cptrs[cc0 + c]
   int cc0;
   double alpha, beta;
 };
 
 struct HssCols {
-  const double** col;         // kept-order columns of Q_sel
-  int32_t* type;              // row support (1: T1 rows, 2: T2 rows, 3: both)
+  const double** col;         // kept-order columns of Q_sel, at the merge's row 0
+  int32_t *lo, *hi;           // rows [lo, hi) where each can be nonzero
   int n1;
 };
 

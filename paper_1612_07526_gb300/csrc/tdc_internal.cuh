@@ -15,34 +15,45 @@ enum : int { ST_SECULAR = 1, ST_NONFINITE = 2, ST_LEAF = 4, ST_WAIT = 8 };
 // Per-sorted-position flags written by the deflation kernel.
 enum : int { F_T1 = 1, F_T2 = 2, F_ROT = 4 };
 
-// One leaf of the DC tree: an nl x nl tridiagonal block solved by one warp.
+// Eigenvector storage.  A problem's top merge (or its only leaf) writes the caller's
+// array in sorted order.  Everything below lives in the problem's pool: three n x n
+// column blocks (ld n) in the workspace, 3n physical columns.  A slot table gives,
+// for every eigenpair slot v of a problem (the eigenpair's index in its node's sorted
+// order, offset by the node's first index), the column holding its eigenvector: a
+// pointer to the column's row 0 of the problem and the rows [lo, hi) where it can be
+// nonzero (the node that produced it).  A deflated column keeps its storage at every
+// level above, so only the top merge moves it.
+
+// One leaf of the DC tree: an nl x nl tridiagonal block.
 struct LeafJob {
-  int64_t v_off;     // first index of the leaf in the d / e / lambda vectors
-  int64_t q_off;     // element offset of the leaf block (0,0) in the output buffer
-  int32_t ld;        // leading dimension of that buffer
-  int32_t buf;       // 0: buffer A, 1: buffer B
+  int64_t v_off;     // first index of the leaf in the d / e / lambda vectors and the slot table
+  int64_t q_off;     // element offset of the leaf block (0,0) in its output array
+  int32_t ld;        // leading dimension of that array
+  int32_t buf;       // 0: the caller's output (the leaf is a whole problem), 1: the pool
   int32_t nl;        // leaf order (1..32)
   int32_t prob;      // problem index
   int32_t root;      // 1 if the leaf is the whole problem (sign convention applied)
-  int32_t pad_;
+  int32_t lo;        // first row of the leaf within its problem
 };
 
-// One rank-one merge (Eqs. 3-6).  The children's eigenvectors are in buffer `src`
-// (0 = A, 1 = B); the merged eigenvectors go to the other buffer.
+// One rank-one merge (Eqs. 3-6) of rows / columns [lo, lo + n1 + n2) of a problem.
 struct MergeJob {
-  int64_t v_off;     // first index of the merged block in the vectors
-  int64_t off_a;     // element offset of block (0,0) in buffer A
-  int64_t off_b;     // ... in buffer B
-  int64_t off_s;     // ... in the side buffer holding rotated columns
-  int64_t lda, ldb, lds;
+  int64_t v_off;     // first index of the merged block in the vectors and the slot table
+  int64_t out_off;   // final merges: element offset of block (0,0) in the caller's output
+  int64_t ld_out;    // leading dimension of the caller's output
+  int64_t pool_off;  // element offset of the problem's pool (3n columns of n rows)
+  int64_t in_off;    // ext merges: element offset of the caller's input block (0,0)
+  int64_t ld_in;     // ext merges: its leading dimension
+  int32_t pn;        // problem order n (the pool's leading dimension)
+  int32_t lo;        // first row / column of the merge within its problem
   int32_t n1, n2;
-  int32_t src;
   int32_t prob;
+  int32_t fin;       // 1: outputs go to the caller's array in sorted order
   double beta;       // coupling entry b_k, used when e_idx < 0
   int64_t e_idx;     // index of b_k in the e vector, or -1
   int64_t mid;       // merge id (index into the per-merge scalars)
-  int32_t root;      // 1 for the top merge of a problem whose output gets the sign convention
-  int32_t pad_;
+  int32_t root;      // 1: the output gets the sign convention (a problem's top merge)
+  int32_t ext;       // 1: the inputs are the caller's block-diagonal Q (tdc_merge), not the slot table
 };
 
 struct MergeScalars {
@@ -68,8 +79,13 @@ struct DevWs {
   int32_t *srcs, *typ, *flag, *ev, *cand, *slot;
   int32_t *kidx, *kperm, *org, *dsrc, *dperm, *posK, *posD;
   int32_t *sval;              // 2n scratch values for the fallback sort
-  const double **colptr;      // grouped (Gu order) non-deflated column pointers
-  const double **dcolptr;     // deflated column pointers
+  const double **colptr;      // grouped (Gu order) non-deflated columns, at the merge's row 0
+  const double **dcolptr;     // deflated columns, at the merge's row 0
+  int32_t *klo, *khi;         // rows [klo, khi) of colptr[k] that can be nonzero (merge rows)
+  int32_t *dlo, *dhi;         // the same for dcolptr[a]
+  double **outptr;            // output column of kept eigenpair i, at the merge's row 0
+  const double **tptr;        // slot table: column pointer at the problem's row 0
+  int32_t *tlo, *thi;         // slot table: nonzero rows [tlo, thi) (problem rows)
   int32_t *rj, *rk;           // rotation records (sorted positions)
   int32_t *chain;             // first rotation of each chain
   double *rc, *rs;
@@ -84,8 +100,44 @@ struct DevWs {
 constexpr int kLeafRot = 2048;   // rotations recorded per leaf (a 32-leaf needs about 1300)
 
 struct QBufs {
-  double *A, *B, *S;          // ping-pong eigenvector buffers and the side buffer
+  double *A;                  // the caller's output array
+  double *P;                  // the pools (workspace)
+  const double *In;           // ext merges: the caller's input array
 };
+
+// Input column j (0 <= j < n1 + n2, the children's sorted order) of a merge: a
+// pointer at the merge's row 0 and the merge rows [lo, hi) where it can be nonzero.
+struct ColRef {
+  const double* p;
+  int lo, hi;
+};
+__device__ __forceinline__ ColRef merge_input(const MergeJob& J, const QBufs& qb, const DevWs& w, int j) {
+  ColRef c;
+  const int m = J.n1 + J.n2;
+  if (J.ext) {
+    c.p = qb.In + J.in_off + (int64_t)j * J.ld_in;
+    c.lo = j < J.n1 ? 0 : J.n1;
+    c.hi = j < J.n1 ? J.n1 : m;
+  } else {
+    const int64_t v = J.v_off + j;
+    c.p = w.tptr[v] + J.lo;
+    c.lo = max(w.tlo[v] - J.lo, 0);
+    c.hi = min(w.thi[v] - J.lo, m);
+  }
+  return c;
+}
+// Column pc (0 <= pc < 3n) of the merge's problem pool, at the merge's row 0.
+__device__ __forceinline__ double* pool_col(const MergeJob& J, const QBufs& qb, int pc) {
+  return qb.P + J.pool_off + (int64_t)pc * J.pn + J.lo;
+}
+// Pool column of a pointer at the merge's row 0, or -1 outside this problem's pool.
+__device__ __forceinline__ int pool_index(const MergeJob& J, const QBufs& qb, const double* p) {
+  const double* base = qb.P + J.pool_off + J.lo;
+  if (p < base) return -1;
+  const int64_t d = p - base;
+  if (d % J.pn != 0 || d / J.pn >= 3 * (int64_t)J.pn) return -1;
+  return (int)(d / J.pn);
+}
 
 // Smallest j with cum[j+1] > b (cum has njobs+1 entries, cum[0] = 0).
 __device__ __forceinline__ int find_job(const int64_t* __restrict__ cum, int njobs, int64_t b) {
