@@ -211,6 +211,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.dlo = c.take<int32_t>(N);
   w.dhi = c.take<int32_t>(N);
   w.outptr = c.take<double*>(N);
+  w.wptr = c.take<double*>(N);
   w.tptr = c.take<const double*>(N);
   w.tlo = c.take<int32_t>(N);
   w.thi = c.take<int32_t>(N);

@@ -2,14 +2,16 @@
 // generated inside the kernel:
 //     U[:, pos_i] = sum_k Q_sel[:, k] Qhat[k, i],
 //     Qhat[k, i]  = zhat_j / ((d_j - d_org(i)) - tau_i) * sinv_i,   j = kperm[k],
+// read from the unscaled columns the norm kernel keeps (one division per entry and
+// merge, not per row tile) and scaled by sinv_i while the tile is loaded,
 // where Q_sel are the non-deflated (possibly rotated) columns in Gu's order
 // (columns touching rows of T1 only, both halves, rows of T2 only).  Rows of T1
 // use the first two groups and rows of T2 the last two, so the zero blocks of
-// diag(Q1, Q2) are never multiplied.  Qhat is never stored.
+// diag(Q1, Q2) are never multiplied.
 //
 // Tile shapes BM x BN x 8 (BM, BN in {32, 64, 128}), 256 threads in a 16 x 16 grid,
 // (BM/16) x (BN/16) FP64 accumulators per thread, double-buffered shared memory;
-// the next slab of Qhat is generated while the current one is consumed.  Every
+// the next slab of Qhat is loaded while the current one is consumed.  Every
 // output element is one FMA chain over k in ascending order, whatever the shape,
 // so all shapes give bit-identical results and the shape is a pure speed choice.
 //
@@ -33,7 +35,8 @@ template <int BM, int BN>
 struct GemmSmem {
   double As[2][BK][BM];
   double Bs[2][BK][BN];
-  double dorg[BN], tau[BN], sinv[BN];
+  double sinv[BN];
+  const double* wcol[BN];
   int pos[BN];
 };
 
@@ -59,8 +62,6 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   const int kbeg = top ? 0 : S.c1;
   const int kend = top ? S.c1 + S.c3 : K;
   const int64_t o = J.v_off;
-  const double* __restrict__ dbar = w.dbar + o;
-  const double* __restrict__ zhat = w.zhat + o;
   const int32_t* __restrict__ kperm = w.kperm + o;
   const double* const* __restrict__ colptr = w.colptr + o;
 
@@ -68,14 +69,12 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   for (int c = tid; c < BN; c += NT) {
     const int i = ct * BN + c;
     if (i < K) {
-      sm.dorg[c] = dbar[w.org[o + i]];
-      sm.tau[c] = w.tau[o + i];
       sm.sinv[c] = w.sinv[o + i];
+      sm.wcol[c] = w.wptr[o + i];
       sm.pos[c] = w.posK[o + i];
     } else {
-      sm.dorg[c] = 0.0;
-      sm.tau[c] = 0.0;
       sm.sinv[c] = 0.0;
+      sm.wcol[c] = nullptr;
       sm.pos[c] = -1;
     }
   }
@@ -104,11 +103,10 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
     const int k = k0 + lb_k;
     if (k < kend) {
       const int j = kperm[k];
-      const double zj = zhat[j], dj = dbar[j];
 #pragma unroll
       for (int u = 0; u < LB; ++u) {
         const int c = lb_c + u;
-        rb[u] = (sm.pos[c] >= 0) ? (zj / ((dj - sm.dorg[c]) - sm.tau[c])) * sm.sinv[c] : 0.0;
+        rb[u] = (sm.pos[c] >= 0) ? sm.wcol[c][j] * sm.sinv[c] : 0.0;
       }
     } else {
 #pragma unroll

@@ -27,14 +27,11 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 // ------------------------------------------------------------------ Qhat entries
 struct QhatSrc {
-  const double* dbar;
-  const double* zhat;
-  const int32_t* org;
-  const double* tau;
+  double* const* wcol;        // unscaled Cauchy columns kept by the norm kernel
   const double* sinv;
 };
 __device__ __forceinline__ double qhat(const QhatSrc& q, int j, int i) {
-  return (q.zhat[j] / ((q.dbar[j] - q.dbar[q.org[i]]) - q.tau[i])) * q.sinv[i];
+  return q.wcol[i][j] * q.sinv[i];
 }
 
 // ------------------------------------------------------------------ batched GEMM
@@ -573,7 +570,7 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   const auto& tree = L.tree;
   auto& nd = L.nd;
   const int64_t o_v = hJ.v_off;
-  QhatSrc q{w.dbar + o_v, w.zhat + o_v, w.org + o_v, w.tau + o_v, w.sinv + o_v};
+  QhatSrc q{w.wptr + o_v, w.sinv + o_v};
   HssCols xc = L.xc;
   xc.n1 = hJ.n1;
   double* const* outp = w.outptr + o_v;     // output column of each kept eigenpair

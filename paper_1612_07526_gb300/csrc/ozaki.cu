@@ -304,11 +304,8 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
   const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
   const int KP = P1 + P3 + P2;
   const int64_t o = J.v_off;
-  const double* __restrict__ dbar = w.dbar + o;
-  const double* __restrict__ zhat = w.zhat + o;
   const int32_t* __restrict__ kperm = w.kperm + o;
-  const double dorg = dbar[w.org[o + i]];
-  const double t = w.tau[o + i];
+  const double* __restrict__ wcol = w.wptr[o + i];     // unscaled column i of the Cauchy factor
   const double si = w.sinv[o + i];
   int e = 0;
   const double cm = w.cmax[o + i];
@@ -323,10 +320,7 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
     const int k = k0 + j;
     const int kg = k < KP ? padded_to_grouped(k, c1, c3, K, P1, P3) : -1;
     double v = 0.0;
-    if (kg >= 0) {
-      const int jj = kperm[kg];
-      v = (zhat[jj] / ((dbar[jj] - dorg) - t)) * si;
-    }
+    if (kg >= 0) v = wcol[kperm[kg]] * si;
     uint16_t tt[S];
     digits_bf16<S>(round_scaled(v, shift), tt);
 #pragma unroll

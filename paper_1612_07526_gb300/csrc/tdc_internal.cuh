@@ -84,6 +84,7 @@ struct DevWs {
   int32_t *klo, *khi;         // rows [klo, khi) of colptr[k] that can be nonzero (merge rows)
   int32_t *dlo, *dhi;         // the same for dcolptr[a]
   double **outptr;            // output column of kept eigenpair i, at the merge's row 0
+  double **wptr;              // column i of the Cauchy factor zhat_j / (d_j - lambda_i), j < K (unscaled)
   const double **tptr;        // slot table: column pointer at the problem's row 0
   int32_t *tlo, *thi;         // slot table: nonzero rows [tlo, thi) (problem rows)
   int32_t *rj, *rk;           // rotation records (sorted positions)
