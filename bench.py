@@ -454,6 +454,13 @@ def main():
                       "kernel": "k_defl_copy: deflated columns to their sorted positions (12 B per entry: live half read, column written)",
                       "peak_source": f"{pk_kind} HBM copy",
                       "algorithmic_per_step": prof.defl_copy_bytes / args.steps})
+    if prof.secular_flops > 0 and prof.ms[2] > 0:
+        cands.append({"bound": "alu", "achieved": prof.secular_flops / (prof.ms[2] * 1e-3) / 1e12,
+                      "peak": fp64_peak, "unit": "TFLOP/s", "ms_per_step": prof.ms[2] / args.steps,
+                      "kernel": "k_secular: secular roots, one warp per root (K terms per evaluation: "
+                                "1 division + 3 FMA)",
+                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                      "algorithmic_per_step": prof.secular_flops / args.steps})
     for c in cands:
         c["frac"] = c["achieved"] / c["peak"] if c["peak"] else None
         c["traffic"] = None

@@ -43,6 +43,7 @@ class TdcProfile(ctypes.Structure):
         ("split_product_flops", ctypes.c_double),
         ("split_tensor_flops", ctypes.c_double),
         ("defl_copy_bytes", ctypes.c_double),
+        ("secular_flops", ctypes.c_double),
     ]
 
 

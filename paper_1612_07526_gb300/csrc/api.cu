@@ -370,6 +370,7 @@ struct ProfState {
   cudaEvent_t open_ev = nullptr;
   int64_t launches[TDC_NPHASE] = {};
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
+  double secular_flops = 0.0;
   int64_t merges = 0, ktot = 0, calls = 0;
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
@@ -427,6 +428,7 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
       if (J.fin) g_prof.copy_bytes += 12.0 * m * (m - K);   // live half read, whole column written
+      g_prof.secular_flops += 7.0 * K * (double)S.evals;      // K terms per evaluation: 1 division, 3 FMA
       g_prof.merges += 1;
       g_prof.ktot += S.K;
     }
@@ -762,7 +764,7 @@ void tdc_profile_begin(void) {
   g_prof.recs.clear();
   for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
   g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
-  g_prof.copy_bytes = 0.0;
+  g_prof.copy_bytes = g_prof.secular_flops = 0.0;
   g_prof.merges = g_prof.ktot = g_prof.calls = 0;
 }
 
@@ -785,6 +787,7 @@ int tdc_profile_end(tdc_profile* out) {
   out->split_product_flops = g_prof.split_flops;
   out->split_tensor_flops = g_prof.tensor_flops;
   out->defl_copy_bytes = g_prof.copy_bytes;
+  out->secular_flops = g_prof.secular_flops;
   g_prof.on = false;
   g_prof.recs.clear();
   g_prof.used = 0;

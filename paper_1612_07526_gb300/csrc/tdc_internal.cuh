@@ -66,6 +66,7 @@ struct MergeScalars {
   int32_t pad_;
   double rho;        // 2 |beta|
   double tol;        // deflation tolerance
+  unsigned long long evals;   // secular-function evaluations over the merge's roots
 };
 
 // Device workspace arrays; per-index arrays are addressed at job.v_off.
