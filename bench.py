@@ -277,6 +277,15 @@ def context_measurements(api, _lib, lib, torch):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # per-phase times of one direct (non-graph) execute of the same plan
+    import ctypes
+    torch.cuda.synchronize()
+    lib.tdc_profile_begin()
+    plan.execute(d_cat, e_cat, lam, q)
+    torch.cuda.synchronize()
+    p = _lib.TdcProfile()
+    lib.tdc_profile_end(ctypes.byref(p))
+    ctx["batched_4096_phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES) if p.ms[i] > 0}
     ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
                            "status_nonzero": int((plan.status != 0).sum()),
                            "tile_shapes": ",".join(map(str, shapes))}
@@ -451,7 +460,7 @@ def main():
     if prof.defl_copy_bytes > 0 and prof.ms[6] > 0:
         cands.append({"bound": "hbm", "achieved": prof.defl_copy_bytes / (prof.ms[6] * 1e-3) / 1e9,
                       "peak": pk["hbm_gbs"], "unit": "GB/s", "ms_per_step": prof.ms[6] / args.steps,
-                      "kernel": "k_defl_copy: deflated columns to their sorted positions (12 B per entry: live half read, column written)",
+                      "kernel": "k_defl_copy: deflated columns gathered to their sorted positions (column written, live rows read)",
                       "peak_source": f"{pk_kind} HBM copy",
                       "algorithmic_per_step": prof.defl_copy_bytes / args.steps})
     if prof.secular_flops > 0 and prof.ms[2] > 0:

@@ -180,8 +180,8 @@ typedef struct tdc_profile {
   double fp64_product_flops;       /* product_flops of the merges on the FP64 product */
   double split_product_flops;      /* product_flops of the merges on the split product */
   double split_tensor_flops;       /* bf16 tensor flops those run: slice pairs x 2 m K K */
-  double defl_copy_bytes;          /* 12 bytes x rows x deflated columns over the top
-                                      merges: the live part read, the column written     */
+  double defl_copy_bytes;          /* top merges: 8 bytes x rows x deflated columns
+                                      written plus 8 bytes x their live rows read         */
   double secular_flops;            /* 7 K x (secular-function evaluations) per merge:
                                       K terms of one division and three FMA each        */
 } tdc_profile;

@@ -276,13 +276,16 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
     const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
     if (prc) return prc;
     bool any_root = false, any_fin = false;
+    int64_t maxm = 0;
     for (const MergeJob& J : lv.jobs) {
       any_root |= J.root != 0;
       any_fin |= J.fin != 0;
+      maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
     }
     // deflated columns move only in a problem's top merge; below, the slot table keeps them in place
     if (any_fin)
-      launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, sign_norm && any_root, st);
+      launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
+                       lv.ccols.back(), maxm, qb, L.w, sign_norm && any_root, st);
   }
   (void)qa_for_sign;
   return 0;
@@ -427,7 +430,7 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
         g_prof.fp64_flops += f;
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
-      if (J.fin) g_prof.copy_bytes += 12.0 * m * (m - K);   // live half read, whole column written
+      if (J.fin) g_prof.copy_bytes += 8.0 * m * (m - K) + 8.0 * (double)S.live;   // columns written, live rows read
       g_prof.secular_flops += 7.0 * K * (double)S.evals;      // K terms per evaluation: 1 division, 3 FMA
       g_prof.merges += 1;
       g_prof.ktot += S.K;
@@ -681,7 +684,8 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
                      qb, L.w, o.max_secular_iter, st);
   const int prc = launch_product(pp, 0, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
   if (prc) return prc;
-  launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), qb, L.w, false, st);
+  launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
+                   lv.ccols.back(), n, qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
   prof_account(P, pp, L.w.scal, st);
   return launch_status();

@@ -67,6 +67,7 @@ struct MergeScalars {
   double rho;        // 2 |beta|
   double tol;        // deflation tolerance
   unsigned long long evals;   // secular-function evaluations over the merge's roots
+  unsigned long long live;    // rows the deflated columns can be nonzero in, summed
 };
 
 // Device workspace arrays; per-index arrays are addressed at job.v_off.
@@ -190,8 +191,14 @@ void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_til
                       QBufs qb, DevWs w, cudaStream_t st);
 int gemm_shape_rows(int cfg);
 int gemm_shape_cols(int cfg);
-void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_cols, int64_t nb_cols,
-                      QBufs qb, DevWs w, bool any_root, cudaStream_t st);
+// Top merges' deflated-column gather and sign convention.  Levels whose largest merge
+// (maxm rows) is below kWideColumn take one warp per column, eight columns per virtual
+// block (the cdiv(m, 8) prefix of the level); larger ones a 256-thread block per column
+// (the m prefix).
+constexpr int64_t kWideColumn = 2048;
+void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
+                      const int64_t* cum_cols, int64_t nb_cols, int64_t maxm, QBufs qb, DevWs w,
+                      bool any_root, cudaStream_t st);
 
 
 constexpr int kGemmShapes = 6;
