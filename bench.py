@@ -286,6 +286,9 @@ def context_measurements(api, _lib, lib, torch):
     p = _lib.TdcProfile()
     lib.tdc_profile_end(ctypes.byref(p))
     ctx["batched_4096_phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES) if p.ms[i] > 0}
+    if p.secular_flops > 0 and p.ms[2] > 0:
+        ctx["batched_4096_secular"] = {"algorithmic_tflop": p.secular_flops / 1e12,
+                                       "achieved_tflops": p.secular_flops / (p.ms[2] * 1e-3) / 1e12}
     ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
                            "status_nonzero": int((plan.status != 0).sum()),
                            "tile_shapes": ",".join(map(str, shapes))}
@@ -466,7 +469,8 @@ def main():
     if prof.secular_flops > 0 and prof.ms[2] > 0:
         cands.append({"bound": "alu", "achieved": prof.secular_flops / (prof.ms[2] * 1e-3) / 1e12,
                       "peak": fp64_peak, "unit": "TFLOP/s", "ms_per_step": prof.ms[2] / args.steps,
-                      "kernel": "k_secular: secular roots, one warp per root (K terms per evaluation: "
+                      "kernel": "k_secular / k_secular_grp: secular roots, a warp per root, or 4-16 lanes "
+                                "per root on levels with enough roots (K terms per evaluation: "
                                 "1 division + 3 FMA)",
                       "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
                       "algorithmic_per_step": prof.secular_flops / args.steps})

@@ -59,7 +59,8 @@ typedef struct tdc_opts {
   int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
                              /* rule), 0..5 = 128x128, 128x64, 64x64, 64x32, 32x32,    */
                              /* 128x32                                                  */
-  int32_t reserved;
+  int32_t secular_lanes;     /* lanes per secular root: 0 = chosen per tree level from  */
+                             /* the level's root count (default), or 4, 8, 16, 32        */
 } tdc_opts;
 
 /* Fills *opts with the defaults listed above. */

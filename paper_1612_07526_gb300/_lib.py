@@ -26,7 +26,7 @@ class TdcOpts(ctypes.Structure):
         ("ozaki_slices", ctypes.c_int32),
         ("max_secular_iter", ctypes.c_int32),
         ("tile_cfg", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("secular_lanes", ctypes.c_int32),
     ]
 
 

@@ -216,6 +216,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.tlo = c.take<int32_t>(N);
   w.thi = c.take<int32_t>(N);
   w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
+  w.lroots = c.take<unsigned long long>(kMaxLevels);
   const size_t NL = (size_t)std::max<int64_t>(nleaf, 1);
   w.lrot = c.take<double2>(NL * kLeafRot);
   w.lroti = c.take<uint8_t>(NL * kLeafRot);
@@ -238,7 +239,9 @@ static tdc_opts resolve_opts(const tdc_opts* o) {
 static bool opts_valid(const tdc_opts& o) {
   return o.path >= TDC_PATH_DENSE_FP64 && o.path <= TDC_PATH_AUTO && o.leaf >= 1 && o.leaf <= 32 &&
          o.max_secular_iter >= 1 && o.ozaki_slices >= 5 && o.ozaki_slices <= 7 && o.hss_leaf >= 16 &&
-         o.hss_rp >= 8 && o.hss_tol > 0.0;
+         o.hss_rp >= 8 && o.hss_tol > 0.0 &&
+         (o.secular_lanes == 0 || o.secular_lanes == 4 || o.secular_lanes == 8 || o.secular_lanes == 16 ||
+          o.secular_lanes == 32);
 }
 
 template <class T>
@@ -260,6 +263,9 @@ static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
 static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const tdc_opts& o,
                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
                     bool sign_norm, double* qa_for_sign, cudaStream_t st) {
+  // leaves of one element and n < 2^31 give at most 31 merge levels
+  static_assert(kMaxLevels >= 32, "level table too small");
+  cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
               o.leaf, d, e, L.w.dmod, nvec, st);
@@ -270,9 +276,9 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
     const int nj = (int)lv.jobs.size();
     if (nj == 0) continue;
     const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
-    launch_merge_level(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
+    launch_merge_level((int)li, jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                        lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
-                       o.max_secular_iter, st);
+                       o.max_secular_iter, o.secular_lanes, st);
     const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
     if (prc) return prc;
     bool any_root = false, any_fin = false;
@@ -679,9 +685,10 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   QBufs qb{Q_out, L.pool, Q};
   const LevelPlan& lv = P.levels[0];
   const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
-  launch_merge_level(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
+  cudaMemsetAsync(L.w.lroots, 0, sizeof(unsigned long long), st);
+  launch_merge_level(0, jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
-                     qb, L.w, o.max_secular_iter, st);
+                     qb, L.w, o.max_secular_iter, o.secular_lanes, st);
   const int prc = launch_product(pp, 0, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
   if (prc) return prc;
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),

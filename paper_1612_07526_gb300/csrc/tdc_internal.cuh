@@ -93,6 +93,7 @@ struct DevWs {
   int32_t *chain;             // first rotation of each chain
   double *rc, *rs;
   MergeScalars *scal;         // per merge id
+  unsigned long long *lroots; // per tree level: non-deflated roots of the level's merges (kMaxLevels)
   double *dmod;               // torn diagonal (Eq. 2 corner updates)
   double2 *lrot;              // leaf QL: recorded plane rotations (c, s), kLeafRot per leaf
   uint8_t *lroti;             // leaf QL: row index i of each rotation (rows i, i+1)
@@ -100,6 +101,7 @@ struct DevWs {
   int *status;                // per problem
 };
 
+constexpr int kMaxLevels = 64;   // merge levels of one plan (log2 of the largest n / leaf, plus one)
 constexpr int kLeafRot = 2048;   // rotations recorded per leaf (a 32-leaf needs about 1300)
 
 struct QBufs {
@@ -180,10 +182,13 @@ void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, i
                  const double* d, const double* e, double* dmod, int64_t ntot, cudaStream_t st);
 void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const double* e,
                    double* lam, QBufs qb, DevWs w, cudaStream_t st);
-void launch_merge_level(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
+// Rank-one merges of one tree level (`lev`, 0 = the lowest; w.lroots zeroed before the
+// first level of a solve).
+// sec_lanes: lanes per secular root, 0 = chosen from the level's root count.
+void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                         const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
-                        int max_iter, cudaStream_t st);
+                        int max_iter, int sec_lanes, cudaStream_t st);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
 // 32x32, 128x32.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
 // tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.

@@ -56,6 +56,11 @@ def test_host_side_argument_checks(lib):
     assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 3, ctypes.byref(o), P(256), 1 << 20, None, None) == -6
     bad = _lib.default_opts(leaf=0)
     assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(bad), P(256), 1 << 20, None, None) == -7
+    assert o.secular_lanes == 0
+    for lanes in (1, 2, 3, 64, -1):
+        bad = _lib.default_opts(secular_lanes=lanes)
+        assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(bad), P(256), 1 << 20,
+                                    None, None) == -7
     assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(o), P(255), 1 << 20, None, None) == -8
     # workspace too small is reported before any launch
     assert lib.tdc_syev_tridiag(64, P(8), P(8), P(8), P(8), 64, ctypes.byref(o), P(256), 16, None, None) == 3
