@@ -260,6 +260,16 @@ int tdc_read_status(const int* dev_status, void* stream);
 /* Library version string. */
 const char* tdc_version(void);
 
+/*
+ * tdc_diag_reciprocal -- diagnostic: r[i] = the reciprocal of x[i] as the secular
+ * sums compute it (Section 1's secular function, one reciprocal per term): Newton-
+ * Raphson on the hardware approximation, within about one unit in the last place of
+ * 1/x for nonzero finite x with |x| <= 2^1022 (larger |x| gives 0).  x, r: n device
+ * doubles.  Asynchronous on `stream`.  Returns 0, -i for a bad argument i, or 4 for a
+ * launch error.
+ */
+int tdc_diag_reciprocal(const double* x, double* r, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
