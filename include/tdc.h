@@ -270,6 +270,13 @@ const char* tdc_version(void);
  */
 int tdc_diag_reciprocal(const double* x, double* r, int64_t n, void* stream);
 
+/*
+ * tdc_diag_rsqrt -- diagnostic: r[i] = 1/sqrt(x[i]) as the leaf QL's plane rotations
+ * compute it (Newton on the hardware approximation), for x in [2^-1020, 2^1020),
+ * within a few units in the last place.  Arguments and returns as tdc_diag_reciprocal.
+ */
+int tdc_diag_rsqrt(const double* x, double* r, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

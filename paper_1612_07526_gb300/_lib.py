@@ -84,6 +84,7 @@ SIGNATURES = [
     ("tdc_profile_end", ctypes.c_int, [ctypes.POINTER(TdcProfile)]),
     ("tdc_version", ctypes.c_char_p, []),
     ("tdc_diag_reciprocal", ctypes.c_int, [_P, _P, _I64, _P]),
+    ("tdc_diag_rsqrt", ctypes.c_int, [_P, _P, _I64, _P]),
 ]
 
 
