@@ -297,6 +297,38 @@ def context_measurements(api, _lib, lib, torch):
     return ctx
 
 
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        else:
+            cpus.add(int(part))
+    return cpus
+
+
+def gpu_local_cpus(torch):
+    """(NUMA node, its CPUs) of the current GPU's PCI device, or (None, None).  Page-locked
+    host buffers allocated by a thread on those CPUs are placed in that node's memory
+    (first touch), next to the GPU's host link."""
+    import subprocess
+    try:
+        idx = torch.cuda.current_device()
+        out = subprocess.run(["nvidia-smi", "-i", str(idx), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, bus, rest = out.split(":")
+        bdf = f"{int(dom, 16):04x}:{bus.lower()}:{rest.lower()}"
+        node = int(open(f"/sys/bus/pci/devices/{bdf}/numa_node").read())
+        if node < 0:
+            return None, None
+        return node, _cpulist(open(f"/sys/devices/system/node/node{node}/cpulist").read())
+    except Exception:
+        return None, None
+
+
 def max_over_ranks(value, dist, device):
     """The largest of the ranks' values (the job's time is the slowest replica's)."""
     import torch
@@ -416,6 +448,12 @@ def main():
     # end to end through the host-memory entry point (pinned buffers)
     e2e = None
     if not args.no_e2e:
+        # host buffers in the memory of the GPU's own NUMA node, as a deployment would
+        # place them (numactl); the node is recorded with the result
+        node, cpus = gpu_local_cpus(torch)
+        old_aff = os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus & old_aff or cpus)
         hs = api.HostSolver(n, opts=opts)
         dh = torch.tensor(d).pin_memory()
         eh = torch.tensor(e).pin_memory()
@@ -427,8 +465,9 @@ def main():
         t1 = time.perf_counter()
         e_max = max_over_ranks((t1 - t0) / args.steps, dist, "cuda")
         e2e = {"value": e_max / world, "unit": "s", "h2d_bytes_per_step": hs.h2d_bytes,
-               "d2h_bytes_per_step": hs.d2h_bytes}
+               "d2h_bytes_per_step": hs.d2h_bytes, "host_numa_node": node}
         del hs
+        os.sched_setaffinity(0, old_aff)
         torch.cuda.empty_cache()
 
     extra = {}

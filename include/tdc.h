@@ -57,8 +57,8 @@ typedef struct tdc_opts {
                              /* FP64-level accuracy for 34 instead of 26 slice products)  */
   int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
   int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
-                             /* rule), 0..5 = 128x128, 128x64, 64x64, 64x32, 32x32,    */
-                             /* 128x32                                                  */
+                             /* rule), 0..7 = 128x128, 128x64, 64x64, 64x32, 32x32,    */
+                             /* 128x32, 64x16, 128x16                                   */
   int32_t secular_lanes;     /* lanes per secular root: 0 = chosen per tree level from  */
                              /* the level's root count (default), or 4, 8, 16, 32        */
 } tdc_opts;
@@ -231,7 +231,7 @@ int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, 
 void tdc_batched_plan_destroy(tdc_batched_plan* plan);
 
 /*
- * Autotuning of the FP64 product's tile shape per DC tree level (the six shapes of
+ * Autotuning of the FP64 product's tile shape per DC tree level (the eight shapes of
  * tdc_opts.tile_cfg).  Every FP64 product sums each output element over k in the
  * same order whatever the shape, so the shape changes speed, never results.
  *

@@ -89,7 +89,7 @@ SIGNATURES = [
 
 
 # FP64 product tile shapes (rows, columns) by tdc_opts.tile_cfg index
-TILE_SHAPES = [(128, 128), (128, 64), (64, 64), (64, 32), (32, 32), (128, 32)]
+TILE_SHAPES = [(128, 128), (128, 64), (64, 64), (64, 32), (32, 32), (128, 32), (64, 16), (128, 16)]
 
 
 def load(path: str = LIB_PATH):

@@ -9,7 +9,8 @@
 // use the first two groups and rows of T2 the last two, so the zero blocks of
 // diag(Q1, Q2) are never multiplied.
 //
-// Tile shapes BM x BN x 8 (BM, BN in {32, 64, 128}), 256 threads in a 16 x 16 grid,
+// Tile shapes BM x BN x 8 (BM in {32, 64, 128}, BN in {16, 32, 64, 128}), 256 threads
+// in a 16 x 16 grid,
 // (BM/16) x (BN/16) FP64 accumulators per thread, double-buffered shared memory;
 // the next slab of Qhat is loaded while the current one is consumed.  Every
 // output element is one FMA chain over k in ascending order, whatever the shape,
@@ -29,7 +30,8 @@ constexpr int BK = 8, NT = 256;
 struct Shape {
   int bm, bn;
 };
-constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32}, {32, 32}, {128, 32}};
+constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32},
+                                        {32, 32},   {128, 32}, {64, 16}, {128, 16}};
 
 template <int BM, int BN>
 struct GemmSmem {
@@ -44,7 +46,8 @@ template <int BM, int BN>
 __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, const MergeJob* __restrict__ jobs,
                                           int njobs, const int64_t* __restrict__ cum, QBufs qb, DevWs w) {
   constexpr int TM = BM / 16, TN = BN / 16;         // accumulators per thread
-  constexpr int LA = BM * BK / NT, LB = BN * BK / NT; // loads / generated entries per thread
+  constexpr int NB = BN * BK;                       // Qhat entries per slab (128 for BN = 16)
+  constexpr int LA = BM * BK / NT, LB = NB >= NT ? NB / NT : 1;  // loads / generated entries per thread
   auto& As = sm.As;
   auto& Bs = sm.Bs;
   const int jb = find_job(cum, njobs, vb);
@@ -82,7 +85,8 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
 
   // loader mapping: thread t covers LA consecutive rows (LB columns) of one k row
   const int la_k = (tid * LA) / BM, la_r = (tid * LA) % BM;
-  const int lb_k = (tid * LB) / BN, lb_c = (tid * LB) % BN;
+  const bool lb_on = tid * LB < NB;                // narrow slabs: the first NB threads
+  const int lb_k = lb_on ? (tid * LB) / BN : 0, lb_c = lb_on ? (tid * LB) % BN : 0;
   double ra[LA], rb[LB];
   auto load_a = [&](int k0) {
     const int k = k0 + la_k;
@@ -101,7 +105,7 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   };
   auto gen_b = [&](int k0) {
     const int k = k0 + lb_k;
-    if (k < kend) {
+    if (lb_on && k < kend) {
       const int j = kperm[k];
 #pragma unroll
       for (int u = 0; u < LB; ++u) {
@@ -116,8 +120,9 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   auto store = [&](int stg) {
 #pragma unroll
     for (int u = 0; u < LA; ++u) As[stg][la_k][la_r + u] = ra[u];
+    if (lb_on)
 #pragma unroll
-    for (int u = 0; u < LB; ++u) Bs[stg][lb_k][lb_c + u] = rb[u];
+      for (int u = 0; u < LB; ++u) Bs[stg][lb_k][lb_c + u] = rb[u];
   };
 
   const int tx = tid & 15, ty = tid >> 4;
@@ -243,7 +248,9 @@ void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_til
     case 2: launch_shape<64, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 3: launch_shape<64, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 4: launch_shape<32, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
-    default: launch_shape<128, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 5: launch_shape<128, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 6: launch_shape<64, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    default: launch_shape<128, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
   }
 }
 

@@ -190,7 +190,7 @@ void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t*
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
                         int max_iter, int sec_lanes, cudaStream_t st);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
-// 32x32, 128x32.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
+// 32x32, 128x32, 64x16, 128x16.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
 // tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.
 void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_tiles, int64_t bound,
                       QBufs qb, DevWs w, cudaStream_t st);
@@ -206,6 +206,6 @@ void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_w8, in
                       bool any_root, cudaStream_t st);
 
 
-constexpr int kGemmShapes = 6;
+constexpr int kGemmShapes = 8;
 
 }  // namespace tdc

@@ -1,5 +1,5 @@
 """FP64 product tile shapes and their autotuner.  Every shape sums each output
-element over k in the same order, so all six shapes must give bit-identical
+element over k in the same order, so all eight shapes must give bit-identical
 eigenpairs; the solve itself is checked against the oracle's pins (Sturm-count
 bisection for the eigenvalues, residual and orthogonality bounds).  The autotuner
 must return valid shapes and leave the results unchanged, for single solves and
@@ -36,7 +36,7 @@ def test_tile_shapes_bit_identical(api, gen, n):
     d, e = _gen(gen, n)
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
     ref = None
-    for cfg in range(6):
+    for cfg in range(len(api._lib.TILE_SHAPES)):
         lam, q = api.syev_tridiag(dt, et, opts={"tile_cfg": cfg})
         if ref is None:
             ref = (lam.clone(), q.clone())
@@ -58,7 +58,7 @@ def test_autotune_single(api):
     lam0, q0 = api.syev_tridiag(dt, et, opts={"tile_cfg": 2})
     shapes = api.autotune(dt, et)
     assert len(shapes) == 6                       # merge levels 64 .. 2048 above leaves of 32
-    assert all(0 <= s < 6 for s in shapes)
+    assert all(0 <= s < 8 for s in shapes)
     lam1, q1 = api.syev_tridiag(dt, et)          # tile_cfg = -1: the tuned shapes
     assert torch.equal(lam0, lam1) and torch.equal(q0, q1)
 
@@ -71,7 +71,7 @@ def test_autotune_batched_plan_graph(api):
     d_cat, e_cat = plan.pack(ds, es)
     lam, q = plan.outputs()
     shapes = plan.autotune(d_cat, e_cat, lam, q)
-    assert len(shapes) >= 1 and all(0 <= s < 6 for s in shapes)
+    assert len(shapes) >= 1 and all(0 <= s < 8 for s in shapes)
     lam_b, q_b, _, _ = api.syev_tridiag_batched(ds, es, opts={"tile_cfg": 0})
     lam2, q2 = plan.outputs()
     plan.capture(d_cat, e_cat, lam2, q2)
