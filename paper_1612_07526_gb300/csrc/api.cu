@@ -266,6 +266,7 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
   // leaves of one element and n < 2^31 give at most 31 merge levels
   static_assert(kMaxLevels >= 32, "level table too small");
   cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.scal, 0, std::max<int64_t>(P.nmerges, 1) * sizeof(MergeScalars), st);
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
               o.leaf, d, e, L.w.dmod, nvec, st);
@@ -686,6 +687,7 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   const LevelPlan& lv = P.levels[0];
   const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
   cudaMemsetAsync(L.w.lroots, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.scal, 0, sizeof(MergeScalars), st);
   launch_merge_level(0, jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
                      qb, L.w, o.max_secular_iter, o.secular_lanes, st);

@@ -68,6 +68,8 @@ struct MergeScalars {
   double tol;        // deflation tolerance
   unsigned long long evals;   // secular-function evaluations over the merge's roots
   unsigned long long live;    // rows the deflated columns can be nonzero in, summed
+  unsigned long long mxbits;  // max(|d|, |z|) as magnitude bits (zeroed per solve)
+  unsigned long long pad2_;
 };
 
 // Device workspace arrays; per-index arrays are addressed at job.v_off.
@@ -182,8 +184,8 @@ void launch_tear(const int64_t* tear_list, const int64_t* tear_ptr, int nprob, i
                  const double* d, const double* e, double* dmod, int64_t ntot, cudaStream_t st);
 void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const double* e,
                    double* lam, QBufs qb, DevWs w, cudaStream_t st);
-// Rank-one merges of one tree level (`lev`, 0 = the lowest; w.lroots zeroed before the
-// first level of a solve).
+// Rank-one merges of one tree level (`lev`, 0 = the lowest; w.lroots and w.scal zeroed
+// before the first level of a solve).  cum_cols: the prefix of the merges' orders.
 // sec_lanes: lanes per secular root, 0 = chosen from the level's root count.
 void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                         const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
