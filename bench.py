@@ -329,6 +329,37 @@ def gpu_local_cpus(torch):
         return None, None
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the timed solve of the
+# default workload (tridiagonal U[-1, 1], n = 32768, FP64 product), from one ncu capture
+# of the default bench command (one pass per launch): bytes per step and launches per
+# step per kernel, with the SHA-256 of the source file the kernel was built from (the
+# capture and its command are summarised under profiles/).  A kernel whose source has
+# changed since reports no traffic.
+TRAFFIC_U32768 = {
+    "k_gemm_fp64": (105_600_000, 10, "paper_1612_07526_gb300/csrc/gemm_fp64.cu", "cf209cc44828bcc6e213924409510e28463ef56048328b18eb355e2e62150381"),
+    "k_secular": (3_300_000, 20, "paper_1612_07526_gb300/csrc/dc_kernels.cu", "d1e92002f3efb00790a87164fef935c42df97c418d3f50a6bcc38b4c5bfcca61"),
+    "k_defl_copy": (8_810_900_000, 1, "paper_1612_07526_gb300/csrc/dc_kernels.cu", "d1e92002f3efb00790a87164fef935c42df97c418d3f50a6bcc38b4c5bfcca61"),
+}
+
+
+def measured_traffic(kernel, args):
+    """(bytes per launch, bytes per step) of `kernel` for the default workload, or None."""
+    import hashlib
+    if (args.n, args.gen, args.path) != (32768, "uniform", "fp64"):
+        return None
+    rec = TRAFFIC_U32768.get(kernel)
+    if rec is None:
+        return None
+    per_step, launches, src, sha = rec
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), src), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return per_step / launches, per_step
+
+
 def max_over_ranks(value, dist, device):
     """The largest of the ranks' values (the job's time is the slowest replica's)."""
     import torch
@@ -515,7 +546,11 @@ def main():
                       "algorithmic_per_step": prof.secular_flops / args.steps})
     for c in cands:
         c["frac"] = c["achieved"] / c["peak"] if c["peak"] else None
-        c["traffic"] = None
+        tr = measured_traffic(c["kernel"].split(":")[0].split(" ")[0], args)
+        c["traffic"] = tr[0] if tr else None
+        if tr:
+            c["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
+            c["traffic_per_step"] = tr[1]
     cands.sort(key=lambda c: -c["ms_per_step"])
     roofline = cands[0] if cands else None
     achieved = (prof.product_flops / ((prof.ms[5] + prof.ms[8] + prof.ms[9]) * 1e-3) / 1e12
