@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the few-deflation and batched context measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the FP64 tile-shape autotuning")
+    ap.add_argument("--direct", action="store_true",
+                    help="time direct tdc_syev_tridiag calls instead of replays of a captured plan")
     return ap.parse_args()
 
 
@@ -443,13 +445,35 @@ def main():
     def step():
         api.syev_tridiag(dt, et, opts=opts, check=False, status=status, out=(lam, q), stream=stream)
 
+    # The timed step is one whole solve.  By default it is the replay of a CUDA graph of
+    # tdc_batched_plan_execute for this one problem (the public entry for repeated solves
+    # of a fixed size: the plan is built, autotuned and captured once, then every step
+    # replays the same kernels on device-resident inputs); --direct times direct
+    # tdc_syev_tridiag calls, with their per-call host work and launches.
     shapes = None
-    if not args.no_tune and args.path in ("fp64", "ozaki"):
-        shapes = api.autotune(dt, et, opts=opts, stream=stream)     # one-time setup, before warm-up
+    plan = None
+    if args.direct:
+        if not args.no_tune and args.path in ("fp64", "ozaki"):
+            shapes = api.autotune(dt, et, opts=opts, stream=stream)     # one-time setup, before warm-up
+        timed = step
+    else:
+        del q
+        torch.cuda.empty_cache()
+        plan = api.BatchedPlan([n], opts=opts)
+        e_cat = torch.zeros(n, dtype=torch.float64, device="cuda")
+        if n > 1:
+            e_cat[:n - 1] = et
+        lam, q_flat = plan.outputs()
+        q = q_flat.view(n, n).t()                                       # column-major n x n
+        if not args.no_tune and args.path in ("fp64", "ozaki"):
+            shapes = plan.autotune(dt, e_cat, lam, q_flat)
+        plan.capture(dt, e_cat, lam, q_flat)
+        timed = plan.replay
     for _ in range(args.warmup):
-        step()
+        timed()
     barrier()
-    bits = lib.tdc_read_status(api._vp(status), api._stream(stream))
+    bits = (int((plan.status != 0).sum()) if plan is not None
+            else lib.tdc_read_status(api._vp(status), api._stream(stream)))
     if bits:
         raise SystemExit(f"device status {bits} during warm-up")
 
@@ -457,24 +481,59 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
-        lib.tdc_profile_begin()
         ev0.record(stream)
         for _ in range(args.steps):
-            step()
+            timed()
         ev1.record(stream)
         ev1.synchronize()
-        prof = _lib.TdcProfile()
-        lib.tdc_profile_end(ctypes.byref(prof))
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max = max_over_ranks(ms, dist, "cuda")
-    bits = lib.tdc_read_status(api._vp(status), api._stream(stream))
+    bits = (int(plan.status.abs().sum()) if plan is not None
+            else lib.tdc_read_status(api._vp(status), api._stream(stream)))
+    # per-phase times, launch and work counts: the same solves again, outside the timed
+    # region, with CUDA events around every phase (direct executes of the same plan)
+    torch.cuda.synchronize()
+    lib.tdc_profile_begin()
+    for _ in range(args.steps):
+        if plan is not None:
+            plan.execute(dt, e_cat, lam, q_flat, stream=stream)
+        else:
+            step()
+    torch.cuda.synchronize()
+    prof = _lib.TdcProfile()
+    lib.tdc_profile_end(ctypes.byref(prof))
+    direct_ms = None
+    if plan is not None:
+        # context: the same solve as direct calls (plan build and launches per call)
+        q_direct = api.fortran_empty(n, n, "cuda")
+        lam_direct = torch.empty(n, dtype=torch.float64, device="cuda")
+        o_direct = _lib.default_opts(path=PATHS[args.path])
+        api.syev_tridiag(dt, et, opts=o_direct, out=(lam_direct, q_direct), stream=stream)
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.steps):
+            api.syev_tridiag(dt, et, opts=o_direct, check=False, out=(lam_direct, q_direct), stream=stream)
+        d1.record(stream)
+        d1.synchronize()
+        direct_ms = d0.elapsed_time(d1) / args.steps
+        del q_direct, lam_direct
+        torch.cuda.empty_cache()
 
     # accuracy of the last solve (sampled columns; the full checks live in the tests)
     acc = {}
     if rank == 0:
         acc = sampled_accuracy(torch, d, e, lam, q)
         acc["status"] = int(bits)
+
+    step_kind = ("direct tdc_syev_tridiag calls" if plan is None else
+                 "replay of a captured CUDA graph of the one-problem batched plan")
+    if plan is not None:
+        del plan, e_cat, q_flat
+    del lam, q
+    torch.cuda.empty_cache()
 
     # end to end through the host-memory entry point (pinned buffers)
     e2e = None
@@ -571,7 +630,9 @@ def main():
                    "n": n, "gen": args.gen, "path": args.path, "leaf": 32,
                    "l2": "inputs and eigenvector buffers (8.6 GB each at n=32768) far exceed L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile_shapes": ("autotuned per level: " + ",".join(map(str, shapes))) if shapes else "size rule"},
+                   "tile_shapes": ("autotuned per level: " + ",".join(map(str, shapes))) if shapes else "size rule",
+                   "step": step_kind,
+                   "direct_call_ms": direct_ms},
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,

@@ -412,6 +412,8 @@ void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
 // After a profiled solve: read the per-merge counts and add up the product's work.
 static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* dscal, cudaStream_t st) {
   if (!g_prof.on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;   // no sync
   const size_t nm = (size_t)std::max<int64_t>(P.nmerges, 1);
   if (g_prof.hscal_n < nm) {
     if (g_prof.hscal) cudaFreeHost(g_prof.hscal);
@@ -876,6 +878,7 @@ int tdc_batched_plan_execute(const tdc_batched_plan* h, const double* d_cat, con
   QBufs qb{Q_cat, L.pool, nullptr};
   const int prc = run_plan(h->P, h->pp, L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, true, Q_cat, st);
   if (prc) return prc;
+  prof_account(h->P, h->pp, L.w.scal, st);
   return launch_status();
 }
 

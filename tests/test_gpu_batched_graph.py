@@ -50,3 +50,24 @@ def test_plan_execute_and_graph_replay(api, path):
         if p % 16 == 0:
             lref, _ = dc.syev(ds[p], es[p])
             assert np.max(np.abs(lp - lref)) <= 10 * n * EPS * metrics.tnorm(ds[p], es[p])
+
+
+@pytest.mark.parametrize("gen,n", [("uniform", 3000), ("toeplitz", 2500)])
+def test_single_problem_plan_matches_direct(api, gen, n):
+    """The one-problem batched plan replayed from a CUDA graph (the bench's timed step)
+    gives the direct solve's eigenpairs bit for bit."""
+    d, e = W.uniform_tridiag(n, 13) if gen == "uniform" else W.toeplitz_121(n)
+    dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
+    lam_d, q_d = api.syev_tridiag(dt, et)
+    plan = api.BatchedPlan([n])
+    e_cat = torch.zeros(n, dtype=torch.float64, device="cuda")
+    e_cat[:n - 1] = et
+    lam, q = plan.outputs()
+    plan.capture(dt, e_cat, lam, q)
+    lam.zero_()
+    q.zero_()
+    plan.replay()
+    torch.cuda.synchronize()
+    assert int(plan.status.abs().sum()) == 0
+    assert torch.equal(lam, lam_d)
+    assert torch.equal(q.view(n, n).t(), q_d)
