@@ -100,6 +100,22 @@ int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host,
                           void* stream);
 
 /*
+ * tdc_syev_tridiag_host_async -- tdc_syev_tridiag_host without the wait: enqueues on
+ * `stream` the copy of d, e in, the solve, and the copies of lambda, Q and the device
+ * status word (to *status_host) out, and returns.  The outputs and *status_host are
+ * valid once the stream has reached that point (synchronize it, or an event recorded
+ * after the call).  Host buffers, status_host included, must be page-locked for the
+ * copies to be asynchronous.  Calls on different streams with different dev_buf run
+ * concurrently, so the copy-out of one problem overlaps the solve of the next.
+ * Returns 0, -i for a bad argument i (-10: status_host NULL), 3 (buffer too small)
+ * or 4 (launch error); the solve's own status arrives in *status_host.
+ */
+int tdc_syev_tridiag_host_async(int64_t n, const double* d_host, const double* e_host,
+                                double* lambda_host, double* Q_host, int64_t ldq,
+                                const tdc_opts* opts, void* dev_buf, size_t dev_buf_bytes,
+                                int* status_host, void* stream);
+
+/*
  * tdc_merge -- one rank-one merge (Eqs. 3-6).  Computes the eigendecomposition of
  *     diag(Q1 D1 Q1^T, Q2 D2 Q2^T) + |beta| v v^T,  v = e_{n1} + sign(beta) e_{n1+1},
  * i.e. D + rho z z^T in the basis Q = diag(Q1, Q2) with rho = 2|beta| and

@@ -62,6 +62,8 @@ SIGNATURES = [
     ("tdc_syev_tridiag", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _OPT, _P, ctypes.c_size_t, _P, _P]),
     ("tdc_host_buffer_bytes", ctypes.c_size_t, [_I64, _OPT]),
     ("tdc_syev_tridiag_host", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _OPT, _P, ctypes.c_size_t, _P]),
+    ("tdc_syev_tridiag_host_async", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _OPT, _P, ctypes.c_size_t, _P,
+                                                   _P]),
     ("tdc_merge_workspace_bytes", ctypes.c_size_t, [_I64, _OPT]),
     ("tdc_merge", ctypes.c_int, [_I64, _I64, _P, _P, _I64, ctypes.c_double, _P, _P, _I64, _P, _OPT,
                                  _P, ctypes.c_size_t, _P, _P]),

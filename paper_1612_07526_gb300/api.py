@@ -238,6 +238,67 @@ class HostSolver:
         return 8 * (self.n + self.n * self.n)
 
 
+class HostPipeline:
+    """A stream of problems of one order n solved from and to host memory with `depth`
+    solves in flight: tdc_syev_tridiag_host_async on `depth` streams, each with its own
+    device buffer and page-locked outputs, so the copy-out of one problem overlaps the
+    solve of the next.  submit() returns the slot holding that problem's result;
+    result(slot) waits for it."""
+
+    def __init__(self, n: int, depth: int = 2, opts=None, device=None):
+        self.lib = _lib.load()
+        self.n = n
+        self.depth = depth
+        self.o = _opts(opts)
+        self.nb = self.lib.tdc_host_buffer_bytes(n, ctypes.byref(self.o))
+        if self.nb == 0:
+            raise ValueError("invalid size or options")
+        dev = device or "cuda"
+        self.bufs = [torch.empty(self.nb, dtype=torch.uint8, device=dev) for _ in range(depth)]
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
+        self.lam = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(depth)]
+        self.q = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(depth)]
+        self.status = torch.zeros(depth, dtype=torch.int32).pin_memory()
+        self.events = [None] * depth
+        self.k = 0
+
+    def _finish(self, s):
+        if self.events[s] is not None:
+            self.events[s].synchronize()
+            self.events[s] = None
+            _raise_status(int(self.status[s]), "tdc_syev_tridiag_host_async")
+
+    def submit(self, d_host: torch.Tensor, e_host: torch.Tensor) -> int:
+        s = self.k % self.depth
+        self.k += 1
+        self._finish(s)                                   # the slot's previous problem
+        st = self.streams[s]
+        rc = self.lib.tdc_syev_tridiag_host_async(
+            self.n, _vp(d_host), _vp(e_host), _vp(self.lam[s]), _vp(self.q[s]), self.n, ctypes.byref(self.o),
+            _vp(self.bufs[s]), self.nb, ctypes.c_void_p(self.status.data_ptr() + 4 * s), _stream(st))
+        _check_rc(rc, "tdc_syev_tridiag_host_async")
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.events[s] = ev
+        return s
+
+    def result(self, s: int):
+        self._finish(s)
+        return self.lam[s], self.q[s].view(self.n, self.n).t()
+
+    def wait_all(self):
+        for s in range(self.depth):
+            self._finish(s)
+
+    @property
+    def h2d_bytes(self):
+        return 8 * (2 * self.n - 1)
+
+    @property
+    def d2h_bytes(self):
+        return 8 * (self.n + self.n * self.n)
+
+
 def syev_backward(lam: torch.Tensor, q: torch.Tensor, g_lam=None, g_q=None, stream=None):
     """(g_d, g_e) of a loss with gradients (g_lam, g_q) at the output (lam, q) of
     syev_tridiag, through tdc_syev_tridiag_backward (band-only adjoint)."""

@@ -580,9 +580,11 @@ size_t tdc_host_buffer_bytes(int64_t n, const tdc_opts* opts) {
   return ws + 3 * vec + mat + 256;
 }
 
-int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host, double* lambda_host,
-                          double* Q_host, int64_t ldq, const tdc_opts* opts, void* dev_buf,
-                          size_t dev_buf_bytes, void* stream) {
+// Checks the host entry's arguments and enqueues copy-in, solve and copy-out on the
+// stream; the status word goes to *status_dst.  Returns 0 or the argument / launch code.
+static int host_enqueue(int64_t n, const double* d_host, const double* e_host, double* lambda_host,
+                        double* Q_host, int64_t ldq, const tdc_opts* opts, void* dev_buf, size_t dev_buf_bytes,
+                        int* status_dst, void* stream) {
   if (n < 1) return -1;
   if (!d_host) return -2;
   if (!e_host && n > 1) return -3;
@@ -605,15 +607,32 @@ int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host,
   void* ws = b + 3 * vec + mat + 256;
   cudaMemcpyAsync(dd, d_host, n * 8, cudaMemcpyHostToDevice, st);
   if (n > 1) cudaMemcpyAsync(de, e_host, (n - 1) * 8, cudaMemcpyHostToDevice, st);
-  int rc = tdc_syev_tridiag(n, dd, de, dl, dq, n, opts, ws, dev_buf_bytes - (3 * vec + mat + 256),
-                            dstat, stream);
+  const int rc = tdc_syev_tridiag(n, dd, de, dl, dq, n, opts, ws, dev_buf_bytes - (3 * vec + mat + 256),
+                                  dstat, stream);
   if (rc != 0) return rc;
   cudaMemcpyAsync(lambda_host, dl, n * 8, cudaMemcpyDeviceToHost, st);
   cudaMemcpy2DAsync(Q_host, ldq * 8, dq, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(status_dst, dstat, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return launch_status();
+}
+
+int tdc_syev_tridiag_host(int64_t n, const double* d_host, const double* e_host, double* lambda_host,
+                          double* Q_host, int64_t ldq, const tdc_opts* opts, void* dev_buf,
+                          size_t dev_buf_bytes, void* stream) {
   int hs = 0;
-  cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
+  const int rc = host_enqueue(n, d_host, e_host, lambda_host, Q_host, ldq, opts, dev_buf, dev_buf_bytes, &hs,
+                              stream);
+  if (rc != 0) return rc;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return 4;
   return hs;
+}
+
+int tdc_syev_tridiag_host_async(int64_t n, const double* d_host, const double* e_host, double* lambda_host,
+                                double* Q_host, int64_t ldq, const tdc_opts* opts, void* dev_buf,
+                                size_t dev_buf_bytes, int* status_host, void* stream) {
+  if (!status_host) return -10;
+  return host_enqueue(n, d_host, e_host, lambda_host, Q_host, ldq, opts, dev_buf, dev_buf_bytes, status_host,
+                      stream);
 }
 
 size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts) {

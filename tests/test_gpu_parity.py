@@ -203,6 +203,29 @@ def test_batched_ragged(api):
         off += n
 
 
+def test_host_pipeline_matches_device_entry(api):
+    """tdc_syev_tridiag_host_async with two solves in flight: every result is the
+    device entry's, bit for bit, including slots reused by later submissions."""
+    n = 500
+    probs = [W.uniform_tridiag(n, 40 + k) for k in range(5)]
+    pipe = api.HostPipeline(n, depth=2)
+    got = []
+    for k, (d, e) in enumerate(probs):
+        slot = pipe.submit(torch.tensor(d).pin_memory(), torch.tensor(np.append(e, 0.0)).pin_memory())
+        if k >= 1:
+            prev = (slot + 1) % 2
+            lam_p, q_p = pipe.result(prev)
+            got.append((k - 1, lam_p.numpy().copy(), q_p.numpy().copy()))
+    lam_p, q_p = pipe.result((len(probs) - 1) % 2)
+    got.append((len(probs) - 1, lam_p.numpy().copy(), q_p.numpy().copy()))
+    pipe.wait_all()
+    assert len(got) == len(probs)
+    for k, lam_h, q_h in got:
+        lam_d, q_d = _solve(api, *probs[k])
+        assert np.array_equal(lam_h, lam_d)
+        assert np.array_equal(q_h, q_d)
+
+
 def test_host_entry_matches_device_entry(api):
     n = 300
     d, e = W.uniform_tridiag(n, 11)
