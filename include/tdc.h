@@ -247,6 +247,25 @@ int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, 
 void tdc_batched_plan_destroy(tdc_batched_plan* plan);
 
 /*
+ * tdc_batched_plan_execute_host -- one execute of the plan between host buffers,
+ * without waiting: enqueues on `stream` the copies of d_host, e_host (the plan's dense
+ * packing, sum(n) doubles each, e padded by one zero per problem) into the caller's
+ * device arrays d_dev, e_dev, the execute (into lambda_dev, Q_dev and dev_status, one
+ * int per problem), and the copies of lambda, Q (sum(n^2) doubles) and the status
+ * words out to lambda_host, Q_host, status_host.  The outputs are valid once the
+ * stream has reached that point.  Host buffers must be page-locked.  The plan was
+ * uploaded at creation, so no pageable copy runs here, and executes of two plans on
+ * two streams overlap the copy-out of one with the solve of the other (a plan and its
+ * device arrays serve one execute at a time).  Returns 0, -i for a bad argument i, or
+ * 4 for a launch error; the solves' status arrives in status_host.
+ */
+int tdc_batched_plan_execute_host(const tdc_batched_plan* plan, const double* d_host,
+                                  const double* e_host, double* lambda_host, double* Q_host,
+                                  int* status_host, double* d_dev, double* e_dev,
+                                  double* lambda_dev, double* Q_dev, int* dev_status,
+                                  void* stream);
+
+/*
  * Autotuning of the FP64 product's tile shape per DC tree level (the eight shapes of
  * tdc_opts.tile_cfg).  Every FP64 product sums each output element over k in the
  * same order whatever the shape, so the shape changes speed, never results.

@@ -240,25 +240,30 @@ class HostSolver:
 
 class HostPipeline:
     """A stream of problems of one order n solved from and to host memory with `depth`
-    solves in flight: tdc_syev_tridiag_host_async on `depth` streams, each with its own
-    device buffer and page-locked outputs, so the copy-out of one problem overlaps the
-    solve of the next.  submit() returns the slot holding that problem's result;
-    result(slot) waits for it."""
+    solves in flight.  Each slot holds a one-problem batched plan (built and uploaded
+    once), its device arrays, page-locked inputs and outputs and a stream; submit()
+    enqueues tdc_batched_plan_execute_host on the slot's stream (copy in, execute, copy
+    out, no pageable copy), so the copy-out of one problem overlaps the solve of the
+    next.  submit() returns the slot holding that problem's result; result(slot) waits
+    for it."""
 
     def __init__(self, n: int, depth: int = 2, opts=None, device=None):
         self.lib = _lib.load()
         self.n = n
         self.depth = depth
-        self.o = _opts(opts)
-        self.nb = self.lib.tdc_host_buffer_bytes(n, ctypes.byref(self.o))
-        if self.nb == 0:
-            raise ValueError("invalid size or options")
         dev = device or "cuda"
-        self.bufs = [torch.empty(self.nb, dtype=torch.uint8, device=dev) for _ in range(depth)]
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
-        self.lam = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(depth)]
-        self.q = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(depth)]
+        self.plans = [BatchedPlan([n], opts=opts, device=dev) for _ in range(depth)]
+        f64 = dict(dtype=torch.float64)
+        self.d_dev = [torch.empty(n, device=dev, **f64) for _ in range(depth)]
+        self.e_dev = [torch.empty(n, device=dev, **f64) for _ in range(depth)]
+        self.lam_dev = [torch.empty(n, device=dev, **f64) for _ in range(depth)]
+        self.q_dev = [torch.empty(n * n, device=dev, **f64) for _ in range(depth)]
+        self.d_in = [torch.empty(n, **f64).pin_memory() for _ in range(depth)]
+        self.e_in = [torch.zeros(n, **f64).pin_memory() for _ in range(depth)]
+        self.lam = [torch.empty(n, **f64).pin_memory() for _ in range(depth)]
+        self.q = [torch.empty(n * n, **f64).pin_memory() for _ in range(depth)]
         self.status = torch.zeros(depth, dtype=torch.int32).pin_memory()
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
         self.events = [None] * depth
         self.k = 0
 
@@ -266,19 +271,24 @@ class HostPipeline:
         if self.events[s] is not None:
             self.events[s].synchronize()
             self.events[s] = None
-            _raise_status(int(self.status[s]), "tdc_syev_tridiag_host_async")
+            _raise_status(int(self.status[s]), "tdc_batched_plan_execute_host")
 
     def submit(self, d_host: torch.Tensor, e_host: torch.Tensor) -> int:
         s = self.k % self.depth
         self.k += 1
         self._finish(s)                                   # the slot's previous problem
-        st = self.streams[s]
-        rc = self.lib.tdc_syev_tridiag_host_async(
-            self.n, _vp(d_host), _vp(e_host), _vp(self.lam[s]), _vp(self.q[s]), self.n, ctypes.byref(self.o),
-            _vp(self.bufs[s]), self.nb, ctypes.c_void_p(self.status.data_ptr() + 4 * s), _stream(st))
-        _check_rc(rc, "tdc_syev_tridiag_host_async")
+        n = self.n
+        self.d_in[s].copy_(torch.as_tensor(d_host, dtype=torch.float64).reshape(-1)[:n])
+        if n > 1:
+            self.e_in[s][:n - 1].copy_(torch.as_tensor(e_host, dtype=torch.float64).reshape(-1)[:n - 1])
+        p = self.plans[s]
+        rc = self.lib.tdc_batched_plan_execute_host(
+            p.handle, _vp(self.d_in[s]), _vp(self.e_in[s]), _vp(self.lam[s]), _vp(self.q[s]),
+            ctypes.c_void_p(self.status.data_ptr() + 4 * s), _vp(self.d_dev[s]), _vp(self.e_dev[s]),
+            _vp(self.lam_dev[s]), _vp(self.q_dev[s]), _vp(p.status), _stream(self.streams[s]))
+        _check_rc(rc, "tdc_batched_plan_execute_host")
         ev = torch.cuda.Event()
-        ev.record(st)
+        ev.record(self.streams[s])
         self.events[s] = ev
         return s
 
@@ -292,7 +302,7 @@ class HostPipeline:
 
     @property
     def h2d_bytes(self):
-        return 8 * (2 * self.n - 1)
+        return 8 * 2 * self.n
 
     @property
     def d2h_bytes(self):

@@ -835,6 +835,7 @@ struct tdc_batched_plan {
   tdc_opts o;
   int32_t batch = 0;
   int64_t vtot = 0;
+  int64_t qtot = 0;
 };
 
 int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts* opts, void* ws,
@@ -862,6 +863,7 @@ int tdc_batched_plan_create(int32_t batch, const int64_t* n_host, const tdc_opts
     qtot += n * n;
   }
   h->vtot = vtot;
+  h->qtot = qtot;
   build_plan(h->P, probs, o.leaf);
   const auto lj = level_jobs(h->P);
   path_prepare(h->pp, o, lj);
@@ -898,6 +900,32 @@ int tdc_batched_plan_execute(const tdc_batched_plan* h, const double* d_cat, con
   const int prc = run_plan(h->P, h->pp, L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, true, Q_cat, st);
   if (prc) return prc;
   prof_account(h->P, h->pp, L.w.scal, st);
+  return launch_status();
+}
+
+int tdc_batched_plan_execute_host(const tdc_batched_plan* h, const double* d_host, const double* e_host,
+                                  double* lambda_host, double* Q_host, int* status_host, double* d_dev,
+                                  double* e_dev, double* lambda_dev, double* Q_dev, int* dev_status,
+                                  void* stream) {
+  if (!h) return -1;
+  if (!d_host) return -2;
+  if (!e_host) return -3;
+  if (!lambda_host) return -4;
+  if (!Q_host) return -5;
+  if (!status_host) return -6;
+  if (!d_dev) return -7;
+  if (!e_dev) return -8;
+  if (!lambda_dev) return -9;
+  if (!Q_dev) return -10;
+  if (!dev_status) return -11;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemcpyAsync(d_dev, d_host, h->vtot * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(e_dev, e_host, h->vtot * sizeof(double), cudaMemcpyHostToDevice, st);
+  const int rc = tdc_batched_plan_execute(h, d_dev, e_dev, lambda_dev, Q_dev, dev_status, stream);
+  if (rc != 0) return rc;
+  cudaMemcpyAsync(lambda_host, lambda_dev, h->vtot * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(Q_host, Q_dev, h->qtot * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(status_host, dev_status, h->batch * sizeof(int), cudaMemcpyDeviceToHost, st);
   return launch_status();
 }
 
