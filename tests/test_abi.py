@@ -66,5 +66,17 @@ def test_host_side_argument_checks(lib):
     assert lib.tdc_syev_tridiag(64, P(8), P(8), P(8), P(8), 64, ctypes.byref(o), P(256), 16, None, None) == 3
     assert lib.tdc_merge(0, 3, P(8), P(8), 3, 1.0, P(8), P(8), 3, None, ctypes.byref(o), P(256), 1 << 20,
                          None, None) == -1
+    # host and pipeline entries: argument checks come before any CUDA call
+    assert lib.tdc_syev_tridiag_host_async(0, P(8), P(8), P(8), P(8), 1, ctypes.byref(o), P(256), 1 << 20,
+                                           P(8), None) == -1
+    assert lib.tdc_syev_tridiag_host_async(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(o), P(256), 1 << 20,
+                                           None, None) == -10
+    assert lib.tdc_syev_tridiag_host_async(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(o), P(255), 1 << 20,
+                                           P(8), None) == -8
+    assert lib.tdc_batched_plan_execute_host(None, P(8), P(8), P(8), P(8), P(8), P(8), P(8), P(8), P(8),
+                                             P(8), None) == -1
+    assert lib.tdc_diag_reciprocal(None, None, -1, None) == -3
+    assert lib.tdc_diag_rsqrt(None, None, -1, None) == -3
+    assert lib.tdc_diag_rsqrt(None, P(8), 4, None) == -1
     assert lib.tdc_workspace_bytes(0, ctypes.byref(o)) == 0
     assert lib.tdc_workspace_bytes(1024, ctypes.byref(o)) > 2 * 1024 * 1024 * 8
