@@ -201,6 +201,8 @@ typedef struct tdc_profile {
                                       written plus 8 bytes x their live rows read         */
   double secular_flops;            /* 7 K x (secular-function evaluations) per merge:
                                       K terms of one division and three FMA each        */
+  int64_t hss_fallbacks;           /* HSS merges whose ID ranks reached the sample count
+                                      (r + p) and that took the dense product instead   */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);

@@ -44,6 +44,7 @@ class TdcProfile(ctypes.Structure):
         ("split_tensor_flops", ctypes.c_double),
         ("defl_copy_bytes", ctypes.c_double),
         ("secular_flops", ctypes.c_double),
+        ("hss_fallbacks", ctypes.c_int64),
     ]
 
 

@@ -381,11 +381,15 @@ struct ProfState {
   int64_t launches[TDC_NPHASE] = {};
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   double secular_flops = 0.0;
-  int64_t merges = 0, ktot = 0, calls = 0;
+  int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0;
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
 };
 static ProfState g_prof;
+
+void hss_fallbacks_add(int n) {
+  if (g_prof.on) g_prof.hss_fallbacks += n;
+}
 
 static cudaEvent_t prof_event() {
   if (g_prof.used == g_prof.pool.size()) {
@@ -799,7 +803,7 @@ void tdc_profile_begin(void) {
   for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
   g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
-  g_prof.merges = g_prof.ktot = g_prof.calls = 0;
+  g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = 0;
 }
 
 int tdc_profile_end(tdc_profile* out) {
@@ -822,6 +826,7 @@ int tdc_profile_end(tdc_profile* out) {
   out->split_tensor_flops = g_prof.tensor_flops;
   out->defl_copy_bytes = g_prof.copy_bytes;
   out->secular_flops = g_prof.secular_flops;
+  out->hss_fallbacks = g_prof.hss_fallbacks;
   g_prof.on = false;
   g_prof.recs.clear();
   g_prof.used = 0;

@@ -552,6 +552,19 @@ size_t hss_arena_bytes(int64_t m, const tdc_opts& o) {
   return L.bytes + 4096;
 }
 
+// 1 in *flag if a node's row or column ID used all rp samples while it had more rows
+// than that: the sampled range may then miss part of the block, and the compression
+// cannot be trusted at the tolerance (the root has no ID).
+__global__ void k_hss_saturated(const HssNodeDev* __restrict__ nd, int nn, int rp, int* __restrict__ flag) {
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const HssNodeDev& d = nd[i];
+    if (d.root) continue;
+    const int ru = d.leaf ? d.hi - d.lo : *d.rows_u;
+    const int rv = d.leaf ? d.hi - d.lo : *d.rows_v;
+    if ((*d.kU >= rp && ru > rp) || (*d.kV >= rp && rv > rp)) atomicOr(flag, 1);
+  }
+}
+
 int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, size_t arena_bytes,
                   const tdc_opts& o, cudaStream_t st) {
   // K is needed on the host to shape the HSS tree
@@ -671,6 +684,14 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     cudaMemcpyAsync(lp, &root, 4, cudaMemcpyHostToDevice, st);
     k_hss_parent<<<1, 256, 0, st>>>(L.dnodes, lp, rp, q);
     lp += 1;
+  }
+  if (nn > 1) {                               // ranks that hit the sample count: dense product instead
+    cudaMemsetAsync(L.dK, 0, sizeof(int), st);
+    k_hss_saturated<<<1, 256, 0, st>>>(L.dnodes, nn, rp, L.dK);
+    int sat = 0;
+    cudaMemcpyAsync(&sat, L.dK, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
+    if (sat) return kHssSaturated;
   }
 
   // ---- multiply: Out = X Qhat_hss, X = Q_sel (m rows, K kept columns)

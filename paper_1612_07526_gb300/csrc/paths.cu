@@ -156,8 +156,13 @@ int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vect
   if (!(L && L->oz)) phase_mark(5, true, 0, st);
   if (L && L->hss) {
     int rc = 0;
-    for (const MergeJob& J : hjobs) {
-      rc = run_hss_merge(J, qb, w, pp.arena_dev, pp.arena_bytes, o, st);
+    for (size_t j = 0; j < hjobs.size(); ++j) {
+      rc = run_hss_merge(hjobs[j], qb, w, pp.arena_dev, pp.arena_bytes, o, st);
+      if (rc == kHssSaturated) {             // samples too few for the ranks: the exact dense product
+        launch_gemm_fp64(L->gemm_cfg, jobs + j, 1, cum_tiles, L->gemm_bound, qb, w, st);
+        hss_fallbacks_add(1);
+        rc = 0;
+      }
       if (rc) break;
     }
     phase_mark(5, false, 1, st);

@@ -80,6 +80,10 @@ void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, siz
 // Runs Algorithm 1 and the HSS multiply for one merge whose deflation, roots,
 // zhat and norms are in w; writes the K non-deflated output columns.  Reads K on the
 // host (one stream synchronization).  Returns 0, 3 (arena too small) or 4.
+// run_hss_merge's return when a node's ID rank reached the sample count (r + p) with
+// more rows than samples: nothing has been written; the caller computes the merge's
+// product densely instead.
+constexpr int kHssSaturated = 100;
 int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, size_t arena_bytes,
                   const tdc_opts& o, cudaStream_t st);
 

@@ -175,6 +175,8 @@ __device__ __forceinline__ double warp_prod(double v) {
 // Profiling hook (defined in api.cu): brackets a phase with CUDA events when the
 // per-phase timing of tdc_profile_begin() is on; a no-op otherwise.
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
+// Counts HSS merges that fell back to the dense product (while profiling is on).
+void hss_fallbacks_add(int n);
 
 // Grid size for a grid-stride kernel: min(nb, SMs x per_sm), at least 1.
 unsigned grid_cap(int64_t nb, int per_sm);

@@ -68,3 +68,38 @@ def test_syev_hss(api, gen, n):
     assert metrics.orthogonality(q) <= 1e-9
     r = metrics.tri_matmul(d, e, q) - q * lam[None, :]
     assert np.linalg.norm(r) <= 1e-9 * nrm * np.sqrt(n)
+
+
+def _profiled(api, fn):
+    import ctypes
+    from paper_1612_07526_gb300 import _lib
+    lib = _lib.load()
+    torch.cuda.synchronize()
+    lib.tdc_profile_begin()
+    out = fn()
+    torch.cuda.synchronize()
+    p = _lib.TdcProfile()
+    lib.tdc_profile_end(ctypes.byref(p))
+    return out, p
+
+
+def test_hss_saturated_ranks_take_dense_product(api):
+    """With r + p = 8 samples the ID ranks of tridiag(1,2,1)'s Cauchy-like Qhat blocks
+    reach the sample count, so every HSS merge (the 15 merges of order >= 2 x 128) takes
+    the dense FP64 product instead: the solve equals the FP64 path bit for bit.  With
+    the default 128 samples no merge falls back."""
+    n = 3000
+    d, e = W.toeplitz_121(n)
+    dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
+    (lam_h, q_h), p = _profiled(api, lambda: api.syev_tridiag(
+        dt, et, opts={"path": 2, "hss_rp": 8, "hss_leaf": 128, "tile_cfg": 2}))
+    assert p.hss_fallbacks == 15
+    lam_f, q_f = api.syev_tridiag(dt, et, opts={"path": 0, "tile_cfg": 2})
+    assert torch.equal(lam_h, lam_f) and torch.equal(q_h, q_f)
+    (lam_d, q_d), p = _profiled(api, lambda: api.syev_tridiag(dt, et, opts={"path": 2, "hss_leaf": 128}))
+    assert p.hss_fallbacks == 0
+    lh, qh = lam_d.cpu().numpy(), q_d.cpu().numpy()
+    nrm = metrics.tnorm(d, e)
+    r = metrics.tri_matmul(d, e, qh) - qh * lh[None, :]
+    assert np.linalg.norm(r) <= 1e-9 * nrm * np.sqrt(n)        # the HSS contract (tolerance 1e-12)
+    assert metrics.orthogonality(qh) <= 1e-9
