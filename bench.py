@@ -452,7 +452,7 @@ def main():
     # tdc_syev_tridiag calls, with their per-call host work and launches.
     shapes = None
     plan = None
-    if args.direct:
+    if args.direct or args.path not in ("fp64", "ozaki"):   # plans cover the dense product paths
         if not args.no_tune and args.path in ("fp64", "ozaki"):
             shapes = api.autotune(dt, et, opts=opts, stream=stream)     # one-time setup, before warm-up
         timed = step
