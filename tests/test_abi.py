@@ -80,3 +80,22 @@ def test_host_side_argument_checks(lib):
     assert lib.tdc_diag_rsqrt(None, P(8), 4, None) == -1
     assert lib.tdc_workspace_bytes(0, ctypes.byref(o)) == 0
     assert lib.tdc_workspace_bytes(1024, ctypes.byref(o)) > 2 * 1024 * 1024 * 8
+
+
+def test_workspace_sizes(lib):
+    """Host-only sizing (no CUDA call): the FP64 workspace is the 3 n^2 pool plus
+    O(n) vectors, the split path adds its slice arena, the host entry adds n^2 for Q
+    and three vectors, a batch needs at least the sum of its problems' pools."""
+    from paper_1612_07526_gb300 import _lib
+    o = _lib.default_opts()
+    for n in (32, 1024, 32768):
+        ws = lib.tdc_workspace_bytes(n, ctypes.byref(o))
+        pool = 3 * n * n * 8
+        assert pool <= ws <= pool + 8 * 1024 * n + (8 << 20)
+        hb = lib.tdc_host_buffer_bytes(n, ctypes.byref(o))
+        assert hb >= ws + n * n * 8 + 3 * n * 8
+    oz = _lib.default_opts(path=1)
+    assert lib.tdc_workspace_bytes(32768, ctypes.byref(oz)) > 1.9 * lib.tdc_workspace_bytes(32768, ctypes.byref(o))
+    sizes = (ctypes.c_int64 * 3)(100, 2000, 32)
+    b = lib.tdc_batched_workspace_bytes(3, sizes, ctypes.byref(o))
+    assert b >= 3 * 8 * (100 ** 2 + 2000 ** 2 + 32 ** 2)
