@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--path", default="fp64", choices=list(PATHS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-n", type=int, default=4096)
+    ap.add_argument("--leaf", type=int, default=32)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the few-deflation and batched context measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the FP64 tile-shape autotuning")
@@ -77,7 +77,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -92,7 +92,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thr = threading.Thread(target=self._read, daemon=True)
             self.thr.start()
         except Exception:
@@ -130,23 +130,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(gen, n_full, n_s):
-    """Times the CPU oracle (as it stands) on an n_s problem of the same distribution and
-    scales by (n_full / n_s)^3 (the DC work is dominated by the n^3 products)."""
-    import numpy as np
-
-    from oracle import dc
-    d, e = make_input(gen, n_s, 0)
-    t0 = time.perf_counter()
-    dc.dc_eig(d, e)
-    t = time.perf_counter() - t0
+def _oracle_threads():
     try:
         import threadpoolctl
         info = threadpoolctl.threadpool_info()
-        cores = max([i.get("num_threads", 1) for i in info] + [1])
+        return max([i.get("num_threads", 1) for i in info] + [1])
     except Exception:
-        cores = os.cpu_count()
-    return t * (n_full / n_s) ** 3, t, cores
+        return os.cpu_count()
+
+
+def time_oracle(gen, n, leaf):
+    """Seconds of one CPU-oracle solve (oracle.dc.dc_eig as it stands) of the workload's
+    matrix of order n."""
+    from oracle import dc
+    d, e = make_input(gen, n, 0)
+    t0 = time.perf_counter()
+    dc.dc_eig(d, e, leaf=leaf)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_fit(gen, n_full, leaf, sizes=(4096, 8192)):
+    """A bounded CPU-oracle sample: solves of orders `sizes` (seed 0, same distribution),
+    timed once each (the CPU has no warm-up effect), and the time at n_full from the
+    power law t = c n^p through the two largest points (p fitted, not assumed)."""
+    import math
+    ts = [time_oracle(gen, n, leaf) for n in sizes]
+    p = math.log(ts[-1] / ts[-2]) / math.log(sizes[-1] / sizes[-2])
+    value = ts[-1] * (n_full / sizes[-1]) ** p
+    sample = ("oracle dc_eig at n=" + ", ".join(f"{n}: {t:.2f} s" for n, t in zip(sizes, ts))
+              + f" ({gen}, seed 0, leaf {leaf}); fitted exponent p={p:.3f}; value = t({sizes[-1]}) x "
+              f"({n_full}/{sizes[-1]})^p")
+    return value, {"sizes": list(sizes), "seconds": ts, "exponent": p}, sample, _oracle_threads()
+
+
+def workload_config(args):
+    """The `config` of both arms' lines (the workload: matrix, order, product path, leaf)."""
+    return {"workload": f"tridiag eig+vecs n={args.n}, {args.gen} seed 0, leaf {args.leaf}, path {args.path}",
+            "n": args.n, "gen": args.gen, "path": args.path, "leaf": args.leaf,
+            "l2": "inputs and eigenvector buffers (8.6 GB each at n=32768) far exceed L2",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
 def sampled_accuracy(torch, d, e, lam, q, ncol=32, seed=1):
@@ -331,35 +353,38 @@ def gpu_local_cpus(torch):
         return None, None
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the timed solve of the
-# default workload (tridiagonal U[-1, 1], n = 32768, FP64 product), from one ncu capture
-# of the default bench command (one pass per launch): bytes per step and launches per
-# step per kernel, with the SHA-256 of the source file the kernel was built from (the
-# capture and its command are summarised under profiles/).  A kernel whose source has
-# changed since reports no traffic.
-TRAFFIC_U32768 = {
-    "k_gemm_fp64": (105_600_000, 10, "paper_1612_07526_gb300/csrc/gemm_fp64.cu", "cf209cc44828bcc6e213924409510e28463ef56048328b18eb355e2e62150381"),
-    "k_secular": (3_300_000, 20, "paper_1612_07526_gb300/csrc/dc_kernels.cu", "d1e92002f3efb00790a87164fef935c42df97c418d3f50a6bcc38b4c5bfcca61"),
-    "k_defl_copy": (8_810_900_000, 1, "paper_1612_07526_gb300/csrc/dc_kernels.cu", "d1e92002f3efb00790a87164fef935c42df97c418d3f50a6bcc38b4c5bfcca61"),
+# DRAM traffic of the FP64 product kernel, from a small case that ncu can capture
+# within its size rule: one solve of tridiag U[-1, 1], n = 8192 (a few GB on the
+# device), DRAM bytes read + written by the three k_gemm_fp64 launches of its top three
+# tree levels, divided by those levels' algorithmic bytes (Q_sel read + U written, the
+# per-level product_min_bytes that the same run records).  The capture and its command
+# are summarised under profiles/.  The product reads each selected column of Q once
+# and writes each output column once whatever n is, so the ratio carries over to
+# n = 32768, where the traffic per launch is the ratio times the algorithmic bytes per
+# launch.  A kernel whose source has changed since the capture reports no traffic.
+TRAFFIC_RATIO = {
+    # levels 5-7 at n = 8192: DRAM 729088 + 369152 + 295424 bytes read, 0 written, against
+    # 9043968 + 9388032 + 9175040 algorithmic bytes (the working set stays in L2)
+    "k_gemm_fp64": (1393664 / 27607040, "paper_1612_07526_gb300/csrc/gemm_fp64.cu",
+                    "cf209cc44828bcc6e213924409510e28463ef56048328b18eb355e2e62150381"),
 }
 
 
-def measured_traffic(kernel, args):
-    """(bytes per launch, bytes per step) of `kernel` for the default workload, or None."""
+def measured_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of `kernel` (the captured ratio times the algorithmic bytes
+    per launch), or None without a capture of the current source."""
     import hashlib
-    if (args.n, args.gen, args.path) != (32768, "uniform", "fp64"):
+    rec = TRAFFIC_RATIO.get(kernel)
+    if rec is None or not alg_bytes_per_launch:
         return None
-    rec = TRAFFIC_U32768.get(kernel)
-    if rec is None:
-        return None
-    per_step, launches, src, sha = rec
+    ratio, src, sha = rec
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), src), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != sha:
                 return None
     except OSError:
         return None
-    return per_step / launches, per_step
+    return ratio * alg_bytes_per_launch
 
 
 def max_over_ranks(value, dist, device):
@@ -378,26 +403,23 @@ def job_seconds_per_solve(step_ms_max, world):
 
 
 def run_reference(args, rank):
+    """The reference arm: the CPU oracle (as it stands) solves the workload's full-size
+    matrix once on the host's cores.  One solve takes minutes, so the arm times exactly
+    one step whatever --steps / --warmup say (a CPU run has no warm-up effect) and
+    reports it with steps = 1, warmup = 0."""
     if rank != 0:
         return
-    vals, samp = [], None
-    for k in range(args.warmup + args.steps):
-        v, t, cores = cpu_oracle_sample(args.gen, args.n, args.cpu_n)
-        if k >= args.warmup:
-            vals.append(v)
-            samp = t
-    value = statistics.mean(vals)
+    t = time_oracle(args.gen, args.n, args.leaf)
+    cores = _oracle_threads()
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1000.0,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"tridiag n={args.n} {args.gen} seed 0 (CPU oracle on an n={args.cpu_n} "
-                               f"sample, scaled by (n/{args.cpu_n})^3)", "n": args.n, "gen": args.gen},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"oracle dc_eig, n={args.cpu_n}, {args.gen}, seed 0: {samp:.2f} s per "
-                                   f"sample, x(n/{args.cpu_n})^3"},
-        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": t, "unit": "s", "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+        "ms_per_step": t * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": t, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": f"the whole workload: one oracle dc_eig solve at n={args.n} ({args.gen}, seed 0, "
+                                   f"leaf {args.leaf}), timed once (no warm-up effect on the CPU)"},
+        "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -436,7 +458,7 @@ def main():
     d, e = make_input(args.gen, n, 0)
     dt = torch.tensor(d, device="cuda")
     et = torch.tensor(e, device="cuda")
-    opts = _lib.default_opts(path=PATHS[args.path])
+    opts = _lib.default_opts(path=PATHS[args.path], leaf=args.leaf)
     lam = torch.empty(n, dtype=torch.float64, device="cuda")
     q = api.fortran_empty(n, n, "cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -508,7 +530,7 @@ def main():
         # context: the same solve as direct calls (plan build and launches per call)
         q_direct = api.fortran_empty(n, n, "cuda")
         lam_direct = torch.empty(n, dtype=torch.float64, device="cuda")
-        o_direct = _lib.default_opts(path=PATHS[args.path])
+        o_direct = _lib.default_opts(path=PATHS[args.path], leaf=args.leaf)
         api.syev_tridiag(dt, et, opts=o_direct, out=(lam_direct, q_direct), stream=stream)
         torch.cuda.synchronize()
         d0 = torch.cuda.Event(enable_timing=True)
@@ -568,6 +590,26 @@ def main():
                "host_numa_node": node}
         del pipe
         torch.cuda.empty_cache()
+        # the bound: the host link's own device-to-host rate for the same bytes, measured
+        # now (one copy of the eigenvector array into page-locked memory, best of three)
+        qd = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        qh = torch.empty(n * n, dtype=torch.float64).pin_memory()
+        best = None
+        for _ in range(4):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            qh.copy_(qd, non_blocking=True)
+            c1.record(stream)
+            c1.synchronize()
+            t = c0.elapsed_time(c1) * 1e-3
+            best = t if best is None else min(best, t)
+        del qd, qh
+        torch.cuda.empty_cache()
+        link = 8.0 * n * n / best
+        e2e["link_d2h_gbs"] = link / 1e9
+        bound_s = e2e["d2h_bytes_per_step"] / link
+        e2e["link_bound_s"] = bound_s
+        e2e["frac_of_link_bound"] = bound_s / e2e["value"]
         # context: one blocking call at a time (tdc_syev_tridiag_host)
         hs = api.HostSolver(n, opts=opts)
         hs(dh, eh)
@@ -624,13 +666,22 @@ def main():
                                 "1 division + 3 FMA)",
                       "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
                       "algorithmic_per_step": prof.secular_flops / args.steps})
+    # per tree level (leaves up), per step: the FP64 product's algorithmic bytes and flops
+    lvl_bytes = [prof.level_fp64_min_bytes[i] / args.steps for i in range(32)]
+    lvl_flops = [prof.level_fp64_flops[i] / args.steps for i in range(32)]
+    nlev = max([i + 1 for i in range(32) if lvl_bytes[i] > 0] + [0])
+    gemm_launches = prof.launches[5] / 2 / args.steps          # k_gemm_sched + k_gemm_fp64 per level
     for c in cands:
         c["frac"] = c["achieved"] / c["peak"] if c["peak"] else None
-        tr = measured_traffic(c["kernel"].split(":")[0].split(" ")[0], args)
-        c["traffic"] = tr[0] if tr else None
-        if tr:
-            c["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
-            c["traffic_per_step"] = tr[1]
+        c["traffic"] = None
+        if c["kernel"].startswith("k_gemm_fp64") and gemm_launches:
+            alg = sum(lvl_bytes) / gemm_launches
+            tr = measured_traffic("k_gemm_fp64", alg)
+            c["algorithmic_bytes_per_launch"] = alg
+            if tr:
+                c["traffic"] = tr
+                c["traffic_unit"] = ("bytes per launch: DRAM read + write per algorithmic byte from the "
+                                     "n=8192 ncu capture, times the algorithmic bytes per launch here")
     cands.sort(key=lambda c: -c["ms_per_step"])
     roofline = cands[0] if cands else None
     achieved = (prof.product_flops / ((prof.ms[5] + prof.ms[8] + prof.ms[9]) * 1e-3) / 1e12
@@ -638,22 +689,17 @@ def main():
 
     cpu = None
     if not args.no_cpu and world == 1:
-        v, t, cores = cpu_oracle_sample(args.gen, n, args.cpu_n)
-        cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle dc_eig at n={args.cpu_n} ({args.gen}, seed 0) took {t:.2f} s; "
-                         f"scaled by (n/{args.cpu_n})^3"}
+        v, fit, sample, cores = cpu_oracle_fit(args.gen, n, args.leaf)
+        cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample, "fit": fit}
 
     line = {
         "metric": METRIC, "value": job_seconds_per_solve(ms_max, world), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"tridiag eig+vecs n={n}, {args.gen} seed 0, leaf 32, path {args.path}",
-                   "n": n, "gen": args.gen, "path": args.path, "leaf": 32,
-                   "l2": "inputs and eigenvector buffers (8.6 GB each at n=32768) far exceed L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile_shapes": ("autotuned per level: " + ",".join(map(str, shapes))) if shapes else "size rule",
-                   "step": step_kind,
-                   "direct_call_ms": direct_ms},
+        "config": workload_config(args),
+        "run": {"tile_shapes": ("autotuned per level: " + ",".join(map(str, shapes))) if shapes else "size rule",
+                "step": step_kind, "direct_call_ms": direct_ms},
+        "fp64_product_levels": {"min_bytes_per_step": lvl_bytes[:nlev], "flops_per_step": lvl_flops[:nlev]},
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,

@@ -137,6 +137,55 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
               void* stream);
 
 /*
+ * tdc_merge_inspect -- tdc_merge, plus a copy of the merge's intermediate values into
+ * caller-provided device arrays, so that each step of the merge can be checked on its
+ * own: the sort of D (the merge of the two ascending halves), deflation (Eq. 5: the
+ * type-1 test on rho |z_j|, the type-2 plane rotations G on nearly equal d_j, and the
+ * permutation P of the deflated entries), the secular roots (Section 1, stored as
+ * (origin, tau) with lambda_i = dbar_origin + tau), the Loewner z of Remark 1 and
+ * the normalisation of the columns of Qhat.  Arguments 1-15 are those of tdc_merge;
+ * `trace` (host struct) holds device pointers, each of which may be NULL (not
+ * copied).  Every array has room for n = n1 + n2 entries; only the prefix that the
+ * counts give is defined.  Indices are 0-based.
+ *   counts[8]  (int64): K, deflated count, plane rotations, Gu groups c1 (columns
+ *              touching rows of T1 only) and c3 (both halves), type-1 deflations,
+ *              then two zeros
+ *   perm[n]    sorted position p -> input index j (ties: the T1 entry first)
+ *   d_sorted, z_sorted [n]: the sorted d and z after the rotations (z scaled by
+ *              1/sqrt(2), rotated entries' d and z updated as Eq. 5's G gives them)
+ *   kept[K], deflated[nd]: sorted positions of the non-deflated and deflated entries,
+ *              ascending
+ *   rot_j, rot_k [nrot], rot_c, rot_s [nrot]: the rotations in the order applied;
+ *              columns (j, k) become (c q_j + s q_k, -s q_j + c q_k)
+ *   dbar, zbar [K]: the non-deflated values
+ *   origin [K] (int32, index into dbar), tau [K]: the roots
+ *   zhat [K]: the Loewner z;  sinv [K]: 1 / ||(D - lambda_i)^{-1} zhat||
+ * Returns as tdc_merge.
+ */
+typedef struct tdc_merge_trace {
+  int64_t* counts;
+  int32_t* perm;
+  double* d_sorted;
+  double* z_sorted;
+  int32_t* kept;
+  int32_t* deflated;
+  int32_t* rot_j;
+  int32_t* rot_k;
+  double* rot_c;
+  double* rot_s;
+  double* dbar;
+  double* zbar;
+  int32_t* origin;
+  double* tau;
+  double* zhat;
+  double* sinv;
+} tdc_merge_trace;
+int tdc_merge_inspect(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq,
+                      double beta, double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out,
+                      const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
+                      void* stream, const tdc_merge_trace* trace);
+
+/*
  * tdc_syev_tridiag_batched -- `batch` independent problems of orders n_host[p]
  * (host array), solved together level by level (one launch per phase per tree level
  * for the whole batch).
@@ -173,6 +222,28 @@ int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, 
                               int* dev_status, void* stream);
 
 /*
+ * tdc_syev_tridiag_backward_batched -- the gradient of tdc_syev_tridiag_backward for
+ * `batch` problems at once (the batched forward's dense packing): problem p has order
+ * n_host[p] (host array), its lambda, g_lambda, g_d and g_e at the prefix sum
+ * n_0 + ... + n_{p-1} of the *_cat vectors (g_e holds n_p - 1 entries there; its
+ * last slot is not written), and its n_p x n_p blocks of Q and Qbar (ld = n_p) at the
+ * prefix sum of n^2 in Q_cat and g_Q_cat.  g_lambda_cat and g_Q_cat may be NULL.  The
+ * nonzero columns of each problem's Qbar are found on the device and counted with one
+ * synchronization of the stream; the products with Q are one batched launch each.
+ * Workspace: tdc_backward_batched_workspace_bytes(batch, n_host, max_cols, opts),
+ * max_cols = the most nonzero columns of any problem's Qbar (-1: any number).
+ * Returns 0, -i for a bad argument i, 3 (workspace too small for the columns
+ * found) or 4 (launch error).
+ */
+size_t tdc_backward_batched_workspace_bytes(int32_t batch, const int64_t* n_host, int64_t max_cols,
+                                            const tdc_opts* opts);
+int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n_host, const double* lambda_cat,
+                                      const double* Q_cat, const double* g_lambda_cat,
+                                      const double* g_Q_cat, double* g_d_cat, double* g_e_cat,
+                                      const tdc_opts* opts, void* ws, size_t ws_bytes,
+                                      int* dev_status, void* stream);
+
+/*
  * Per-phase device timing.  Between tdc_profile_begin() and tdc_profile_end(), every
  * solve records a pair of CUDA events on its own stream around each phase of each
  * tree level, and synchronizes its stream once at its end to read back the
@@ -185,6 +256,7 @@ int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, 
  * Not thread-safe; meant for benchmarks.
  */
 #define TDC_NPHASE 10
+#define TDC_PROFILE_LEVELS 32
 typedef struct tdc_profile {
   double ms[TDC_NPHASE];           /* summed event time per phase                     */
   int64_t launches[TDC_NPHASE];    /* kernel launches per phase                       */
@@ -203,6 +275,9 @@ typedef struct tdc_profile {
                                       K terms of one division and three FMA each        */
   int64_t hss_fallbacks;           /* HSS merges whose ID ranks reached the sample count
                                       (r + p) and that took the dense product instead   */
+  double level_fp64_min_bytes[TDC_PROFILE_LEVELS];   /* per tree level (leaves up): the
+                                      product_min_bytes of its merges on the FP64 product */
+  double level_fp64_flops[TDC_PROFILE_LEVELS];       /* the same for fp64_product_flops  */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);

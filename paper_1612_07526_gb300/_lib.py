@@ -45,7 +45,16 @@ class TdcProfile(ctypes.Structure):
         ("defl_copy_bytes", ctypes.c_double),
         ("secular_flops", ctypes.c_double),
         ("hss_fallbacks", ctypes.c_int64),
+        ("level_fp64_min_bytes", ctypes.c_double * 32),
+        ("level_fp64_flops", ctypes.c_double * 32),
     ]
+
+
+class TdcMergeTrace(ctypes.Structure):
+    """Device pointers receiving a merge's intermediate values (tdc_merge_inspect)."""
+    _fields_ = [(name, ctypes.c_void_p) for name in (
+        "counts", "perm", "d_sorted", "z_sorted", "kept", "deflated", "rot_j", "rot_k", "rot_c", "rot_s",
+        "dbar", "zbar", "origin", "tau", "zhat", "sinv")]
 
 
 PHASES = ["tear+leaves", "deflation", "secular", "lowner+norms", "placement", "product",
@@ -68,6 +77,8 @@ SIGNATURES = [
     ("tdc_merge_workspace_bytes", ctypes.c_size_t, [_I64, _OPT]),
     ("tdc_merge", ctypes.c_int, [_I64, _I64, _P, _P, _I64, ctypes.c_double, _P, _P, _I64, _P, _OPT,
                                  _P, ctypes.c_size_t, _P, _P]),
+    ("tdc_merge_inspect", ctypes.c_int, [_I64, _I64, _P, _P, _I64, ctypes.c_double, _P, _P, _I64, _P, _OPT,
+                                         _P, ctypes.c_size_t, _P, _P, ctypes.POINTER(TdcMergeTrace)]),
     ("tdc_batched_workspace_bytes", ctypes.c_size_t, [ctypes.c_int32, _P, _OPT]),
     ("tdc_syev_tridiag_batched", ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _OPT, _P,
                                                 ctypes.c_size_t, _P, _P]),
@@ -80,6 +91,9 @@ SIGNATURES = [
     ("tdc_batched_plan_execute_host", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("tdc_syev_tridiag_backward", ctypes.c_int, [_I64, _P, _P, _I64, _P, _P, _I64, _P, _P, _OPT, _P,
                                                  ctypes.c_size_t, _P, _P]),
+    ("tdc_backward_batched_workspace_bytes", ctypes.c_size_t, [ctypes.c_int32, _P, _I64, _OPT]),
+    ("tdc_syev_tridiag_backward_batched", ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _OPT, _P,
+                                                         ctypes.c_size_t, _P, _P]),
     ("tdc_syev_tridiag_noalloc", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
     ("tdc_autotune", ctypes.c_int, [_I64, _P, _P, _P, _P, _I64, _OPT, _P, ctypes.c_size_t, _P, ctypes.c_int32,
                                     _P, _P, _P]),

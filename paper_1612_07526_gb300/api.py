@@ -159,6 +159,48 @@ def merge(D: torch.Tensor, Q: torch.Tensor, n1: int, beta: float, opts=None, str
     return lam, qo, int(kout.item()) if check else kout
 
 
+TRACE_INT32 = ("perm", "kept", "deflated", "rot_j", "rot_k", "origin")
+
+
+def merge_inspect(D: torch.Tensor, Q: torch.Tensor, n1: int, beta: float, opts=None, stream=None):
+    """tdc_merge plus the merge's intermediate values (tdc_merge_inspect).  Returns
+    (lam, Q_out, trace) with trace a dict of host numpy arrays cut to their defined
+    lengths: counts (K, nd, nrot, c1, c3, type-1 count), perm, d_sorted, z_sorted,
+    kept, deflated, rot_j, rot_k, rot_c, rot_s, dbar, zbar, origin, tau, zhat, sinv."""
+    lib = _lib.load()
+    n = int(D.shape[0])
+    assert Q.stride() == (1, n) and Q.shape == (n, n) and Q.dtype == torch.float64
+    o = _opts(opts)
+    dev = D.device
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    qo = fortran_empty(n, n, dev)
+    bufs = {"counts": torch.zeros(8, dtype=torch.int64, device=dev)}
+    tr = _lib.TdcMergeTrace()
+    for name, _ in _lib.TdcMergeTrace._fields_:
+        if name == "counts":
+            continue
+        bufs[name] = torch.zeros(n, dtype=torch.int32 if name in TRACE_INT32 else torch.float64, device=dev)
+    for name, t in bufs.items():
+        setattr(tr, name, t.data_ptr())
+    nb = lib.tdc_merge_workspace_bytes(n, ctypes.byref(o))
+    if nb == 0:
+        raise ValueError("invalid size or options")
+    ws = workspace(nb, dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    rc = lib.tdc_merge_inspect(int(n1), int(n - n1), _vp(D), _vp(Q), n, float(beta), _vp(lam), _vp(qo), n,
+                               None, ctypes.byref(o), _vp(ws), ws.numel(), _vp(st), _stream(stream),
+                               ctypes.byref(tr))
+    _check_rc(rc, "tdc_merge_inspect")
+    _raise_status(lib.tdc_read_status(_vp(st), _stream(stream)), "tdc_merge_inspect")
+    h = {k: v.cpu().numpy() for k, v in bufs.items()}
+    K, nd, nrot = int(h["counts"][0]), int(h["counts"][1]), int(h["counts"][2])
+    cut = {"perm": n, "d_sorted": n, "z_sorted": n, "kept": K, "deflated": nd, "rot_j": nrot, "rot_k": nrot,
+           "rot_c": nrot, "rot_s": nrot, "dbar": K, "zbar": K, "origin": K, "tau": K, "zhat": K, "sinv": K}
+    for k, m in cut.items():
+        h[k] = h[k][:m]
+    return lam, qo, h
+
+
 def syev_tridiag_batched(ds, es, opts=None, stream=None, check: bool = True):
     """Solves len(ds) independent problems in one level-synchronous sweep.
 

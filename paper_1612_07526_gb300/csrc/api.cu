@@ -382,13 +382,21 @@ struct ProfState {
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   double secular_flops = 0.0;
   int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0;
+  double lvl_bytes[TDC_PROFILE_LEVELS] = {}, lvl_flops[TDC_PROFILE_LEVELS] = {};
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
 };
 static ProfState g_prof;
 
+// Calls that must not create events (the allocation-free entry) suspend the per-phase
+// marks on their thread for their duration.
+static thread_local bool t_prof_suspended = false;
+ProfileSuspend::ProfileSuspend(bool on) : prev_(t_prof_suspended) { t_prof_suspended = prev_ || on; }
+ProfileSuspend::~ProfileSuspend() { t_prof_suspended = prev_; }
+
+
 void hss_fallbacks_add(int n) {
-  if (g_prof.on) g_prof.hss_fallbacks += n;
+  if (g_prof.on && !t_prof_suspended) g_prof.hss_fallbacks += n;
 }
 
 static cudaEvent_t prof_event() {
@@ -401,7 +409,7 @@ static cudaEvent_t prof_event() {
 }
 
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
-  if (!g_prof.on) return;
+  if (!g_prof.on || t_prof_suspended) return;
   if (begin) {
     g_prof.open_ev = prof_event();
     cudaEventRecord(g_prof.open_ev, st);
@@ -441,6 +449,10 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
         g_prof.tensor_flops += pairs * f;
       } else if (!hss) {
         g_prof.fp64_flops += f;
+        if (l < TDC_PROFILE_LEVELS) {
+          g_prof.lvl_flops[l] += f;
+          g_prof.lvl_bytes[l] += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
+        }
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
       if (J.fin) g_prof.copy_bytes += 8.0 * m * (m - K) + 8.0 * (double)S.live;   // columns written, live rows read
@@ -488,6 +500,7 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   if (!opts_valid(o) || !path_supported(o)) return -7;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -8;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const ProfileSuspend no_events(!profile_accounting);   // no per-phase events either
   Plan P;
   single_problem_plan(P, n, ldq, o.leaf);
   PathPlan pp;
@@ -504,6 +517,55 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   if (prc) return prc;
   if (profile_accounting) prof_account(P, pp, L.w.scal, st);
   return launch_status();
+}
+
+// Intermediate values of one merge (tdc_merge_inspect): the per-merge counts from the
+// merge scalars and the type-1 flags, and copies of the per-index arrays, all read
+// from the workspace after the merge's kernels (in stream order).
+__global__ void k_trace_counts(const MergeScalars* __restrict__ scal, const int32_t* __restrict__ flag,
+                               int m, int64_t* __restrict__ out) {
+  __shared__ int s_t1;
+  if (threadIdx.x == 0) s_t1 = 0;
+  __syncthreads();
+  int c = 0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) c += (flag[p] & F_T1) != 0;
+  atomicAdd(&s_t1, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const MergeScalars S = scal[0];
+    out[0] = S.K;
+    out[1] = S.nd;
+    out[2] = S.nrot;
+    out[3] = S.c1;
+    out[4] = S.c3;
+    out[5] = s_t1;
+    out[6] = 0;
+    out[7] = 0;
+  }
+}
+
+template <class T>
+static void trace_copy(T* dst, const T* src, int64_t n, cudaStream_t st) {
+  if (dst) cudaMemcpyAsync(dst, src, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+}
+
+static void copy_trace(const tdc_merge_trace& t, const DevWs& w, int64_t n, cudaStream_t st) {
+  if (t.counts) k_trace_counts<<<1, 256, 0, st>>>(w.scal, w.flag, (int)n, t.counts);
+  trace_copy(t.perm, w.srcs, n, st);
+  trace_copy(t.d_sorted, w.ds, n, st);
+  trace_copy(t.z_sorted, w.zs, n, st);
+  trace_copy(t.kept, w.kidx, n, st);
+  trace_copy(t.deflated, w.dsrc, n, st);
+  trace_copy(t.rot_j, w.rj, n, st);
+  trace_copy(t.rot_k, w.rk, n, st);
+  trace_copy(t.rot_c, w.rc, n, st);
+  trace_copy(t.rot_s, w.rs, n, st);
+  trace_copy(t.dbar, w.dbar, n, st);
+  trace_copy(t.zbar, w.zbar, n, st);
+  trace_copy(t.origin, w.org, n, st);
+  trace_copy(t.tau, w.tau, n, st);
+  trace_copy(t.zhat, w.zhat, n, st);
+  trace_copy(t.sinv, w.sinv, n, st);
 }
 
 }  // namespace tdc
@@ -657,9 +719,9 @@ size_t tdc_merge_workspace_bytes(int64_t n, const tdc_opts* opts) {
   return L.bytes;
 }
 
-int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq, double beta,
-              double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out, const tdc_opts* opts,
-              void* ws, size_t ws_bytes, int* dev_status, void* stream) {
+static int merge_core(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq, double beta,
+                      double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out, const tdc_opts* opts,
+                      void* ws, size_t ws_bytes, int* dev_status, void* stream, const tdc_merge_trace* tr) {
   if (n1 < 1) return -1;
   if (n2 < 1) return -2;
   if (!D) return -3;
@@ -721,8 +783,24 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
                    lv.ccols.back(), n, qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
+  if (tr) copy_trace(*tr, L.w, n, st);
   prof_account(P, pp, L.w.scal, st);
   return launch_status();
+}
+
+int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq, double beta,
+              double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out, const tdc_opts* opts,
+              void* ws, size_t ws_bytes, int* dev_status, void* stream) {
+  return merge_core(n1, n2, D, Q, ldq, beta, lambda, Q_out, ldqo, K_out, opts, ws, ws_bytes, dev_status,
+                    stream, nullptr);
+}
+
+int tdc_merge_inspect(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq, double beta,
+                      double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out, const tdc_opts* opts,
+                      void* ws, size_t ws_bytes, int* dev_status, void* stream, const tdc_merge_trace* trace) {
+  if (!trace) return -16;
+  return merge_core(n1, n2, D, Q, ldq, beta, lambda, Q_out, ldqo, K_out, opts, ws, ws_bytes, dev_status,
+                    stream, trace);
 }
 
 size_t tdc_batched_workspace_bytes(int32_t batch, const int64_t* n_host, const tdc_opts* opts) {
@@ -804,6 +882,7 @@ void tdc_profile_begin(void) {
   g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
   g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = 0;
+  for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) g_prof.lvl_bytes[l] = g_prof.lvl_flops[l] = 0.0;
 }
 
 int tdc_profile_end(tdc_profile* out) {
@@ -827,6 +906,10 @@ int tdc_profile_end(tdc_profile* out) {
   out->defl_copy_bytes = g_prof.copy_bytes;
   out->secular_flops = g_prof.secular_flops;
   out->hss_fallbacks = g_prof.hss_fallbacks;
+  for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) {
+    out->level_fp64_min_bytes[l] = g_prof.lvl_bytes[l];
+    out->level_fp64_flops[l] = g_prof.lvl_flops[l];
+  }
   g_prof.on = false;
   g_prof.recs.clear();
   g_prof.used = 0;

@@ -11,11 +11,14 @@
 // tree is stored: (lambda, Q) are all the backward needs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cstring>
 #include <vector>
 
 #include "../../include/tdc.h"
 #include "tdc_hss.cuh"
+#include "tdc_internal.cuh"
 
 namespace tdc {
 namespace {
@@ -83,6 +86,147 @@ __global__ void k_bw_band(const double* __restrict__ Q, int64_t ld, int64_t n, c
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
+// ---------------------------------------------------------------- batched form
+// Problem p of a batch: order n, its vectors at v (dense packing: prefix sums of n)
+// and its n x n blocks at q (prefix sums of n^2, ld = n); after the column count, its
+// s nonzero columns of Qbar are listed at c (prefix sums of n) and its n x s blocks
+// G, P, W start at g (prefix sums of n s).
+struct BwProb {
+  int64_t n, v, q, g;
+  int32_t s, pad_;
+};
+
+// Column j of the batch (prefix of n): 1 if Qbar's column is nonzero anywhere.
+__global__ void k_bwb_flag(const BwProb* __restrict__ pr, int nb, const int64_t* __restrict__ cum_n,
+                           const double* __restrict__ gq, int* __restrict__ flag) {
+  const int p = find_job(cum_n, nb, blockIdx.x);
+  const int64_t c = blockIdx.x - cum_n[p];
+  const BwProb P = pr[p];
+  bool nz = false;
+  for (int64_t r = threadIdx.x; r < P.n; r += blockDim.x) nz |= gq[P.q + c * P.n + r] != 0.0;
+  nz = __syncthreads_or(nz);
+  if (threadIdx.x == 0) flag[P.v + c] = nz ? 1 : 0;
+}
+
+// One block per problem: the nonzero columns in ascending order and their count.
+__global__ void k_bwb_compact(BwProb* __restrict__ pr, const int* __restrict__ flag, int* __restrict__ cols) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  BwProb& P = pr[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < P.n; c0 += blockDim.x) {
+    const int64_t c = c0 + tid;
+    const int f = c < P.n ? flag[P.v + c] : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_warp[wid] = __popc(b);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      before += w2 < wid ? s_warp[w2] : 0;
+      total += s_warp[w2];
+    }
+    if (f) cols[P.v + s_base + before + __popc(b & ((1u << lane) - 1u))] = (int)c;
+    __syncthreads();
+    if (tid == 0) s_base += total;
+    __syncthreads();
+  }
+  if (tid == 0) P.s = s_base;
+}
+
+// G(:, k) = Qbar(:, cols[k]) for every problem: element e of the batch's n s prefix.
+__global__ void k_bwb_gather(const BwProb* __restrict__ pr, int nb, const int64_t* __restrict__ cum_ns,
+                             int64_t total, const double* __restrict__ gq, const int* __restrict__ cols,
+                             double* __restrict__ G) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = find_job(cum_ns, nb, e);
+    const BwProb P = pr[p];
+    const int64_t l = e - cum_ns[p];
+    const int64_t r = l % P.n, k = l / P.n;
+    G[P.g + l] = gq[P.q + (int64_t)cols[P.v + k] * P.n + r];
+  }
+}
+
+// M(i, k) = P(i, k) / (lambda_{cols[k]} - lambda_i), zero for i = cols[k] (overwrites G).
+__global__ void k_bwb_m(const BwProb* __restrict__ pr, int nb, const int64_t* __restrict__ cum_ns, int64_t total,
+                        const double* __restrict__ Pm, const double* __restrict__ lam, const int* __restrict__ cols,
+                        double* __restrict__ M) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = find_job(cum_ns, nb, e);
+    const BwProb P = pr[p];
+    const int64_t l = e - cum_ns[p];
+    const int64_t i = l % P.n, k = l / P.n;
+    const int c = cols[P.v + k];
+    M[P.g + l] = (i == c) ? 0.0 : Pm[P.g + l] / (lam[P.v + c] - lam[P.v + i]);
+  }
+}
+
+// The band of Tbar, one row a of one problem per thread (the batch's n prefix).
+__global__ void k_bwb_band(const BwProb* __restrict__ pr, int nb, const int64_t* __restrict__ cum_n, int64_t total,
+                           const double* __restrict__ Q, const double* __restrict__ glam,
+                           const double* __restrict__ W, const int* __restrict__ cols, double* __restrict__ gd,
+                           double* __restrict__ ge) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int p = find_job(cum_n, nb, e);
+  const BwProb P = pr[p];
+  const int64_t a = e - cum_n[p], n = P.n;
+  const double* Qp = Q + P.q;
+  const bool has_next = a + 1 < n;
+  double dsum = 0.0, esum = 0.0;
+  if (glam) {
+    const double* gl = glam + P.v;
+    for (int64_t i = 0; i < n; ++i) {
+      const double qa = Qp[i * n + a];
+      dsum += gl[i] * qa * qa;
+      if (has_next) esum += gl[i] * qa * Qp[i * n + a + 1];
+    }
+    esum *= 2.0;
+  }
+  const double* Wp = W + P.g;
+  for (int k = 0; k < P.s; ++k) {
+    const int64_t col = cols[P.v + k];
+    const double wa = Wp[(int64_t)k * n + a];
+    const double qa = Qp[col * n + a];
+    dsum += wa * qa;
+    if (has_next) esum += wa * Qp[col * n + a + 1] + Wp[(int64_t)k * n + a + 1] * qa;
+  }
+  gd[P.v + a] = dsum;
+  if (has_next) ge[P.v + a] = esum;
+}
+
+constexpr size_t kBwTab = size_t(1) << 22;     // GEMM job tables (the batched GEMM's limit)
+
+struct BwLayout {
+  BwProb* prob;
+  int64_t* cum;          // cum_n (nb + 1), then cum_ns (nb + 1)
+  int* flag;
+  int* cols;
+  unsigned char* tab;
+  double* G;             // sum n s each: G (then M), P, W
+  double* P;
+  double* W;
+  size_t fixed;          // bytes before G
+};
+
+BwLayout bw_layout(unsigned char* b, int nb, int64_t vtot) {
+  BwLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = b ? b + off : nullptr;
+    off = al(off + bytes);
+    return p;
+  };
+  L.prob = reinterpret_cast<BwProb*>(take(sizeof(BwProb) * nb));
+  L.cum = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * 2 * (nb + 1)));
+  L.flag = reinterpret_cast<int*>(take(sizeof(int) * vtot));
+  L.cols = reinterpret_cast<int*>(take(sizeof(int) * vtot));
+  L.tab = take(kBwTab);
+  L.fixed = off;
+  return L;
+}
+
 }  // namespace
 }  // namespace tdc
 
@@ -149,5 +293,109 @@ extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const 
     launch_dense_gemms(g, tab, toff, st);
   }
   k_bw_band<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Q, ldq, n, lambda, g_lambda, W, cols, s, g_d, g_e);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+
+extern "C" size_t tdc_backward_batched_workspace_bytes(int32_t batch, const int64_t* n_host, int64_t max_cols,
+                                                       const tdc_opts* opts) {
+  (void)opts;
+  if (batch < 1 || !n_host) return 0;
+  int64_t vtot = 0, ns = 0;
+  for (int p = 0; p < batch; ++p) {
+    if (n_host[p] < 1) return 0;
+    vtot += n_host[p];
+    const int64_t s = max_cols < 0 ? n_host[p] : std::min<int64_t>(max_cols, n_host[p]);
+    ns += n_host[p] * std::max<int64_t>(s, 1);
+  }
+  const BwLayout L = bw_layout(nullptr, batch, vtot);
+  return L.fixed + 3 * al((size_t)ns * 8) + 256;
+}
+
+extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n_host, const double* lambda_cat,
+                                                 const double* Q_cat, const double* g_lambda_cat,
+                                                 const double* g_Q_cat, double* g_d_cat, double* g_e_cat,
+                                                 const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
+                                                 void* stream) {
+  (void)opts;
+  (void)dev_status;
+  if (batch < 1) return -1;
+  if (!n_host) return -2;
+  if (!lambda_cat) return -3;
+  if (!Q_cat) return -4;
+  if (!g_d_cat) return -7;
+  if (!g_e_cat) return -8;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return -10;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<BwProb> pr(batch);
+  std::vector<int64_t> cum(2 * (batch + 1), 0);
+  int64_t vtot = 0, qtot = 0;
+  for (int p = 0; p < batch; ++p) {
+    const int64_t n = n_host[p];
+    if (n < 1 || n > INT32_MAX) return -2;
+    pr[p] = BwProb{n, vtot, qtot, 0, 0, 0};
+    vtot += n;
+    qtot += n * n;
+    cum[p + 1] = cum[p] + n;
+  }
+  unsigned char* b = reinterpret_cast<unsigned char*>(ws);
+  BwLayout L = bw_layout(b, batch, vtot);
+  if (L.fixed + 256 > ws_bytes) return 3;
+  if (g_Q_cat) {
+    cudaMemcpyAsync(L.prob, pr.data(), sizeof(BwProb) * batch, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(L.cum, cum.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, st);
+    if (vtot > 0x7FFFFFFF) return -2;
+    k_bwb_flag<<<(unsigned)vtot, 256, 0, st>>>(L.prob, batch, L.cum, g_Q_cat, L.flag);
+    k_bwb_compact<<<batch, 256, 0, st>>>(L.prob, L.flag, L.cols);
+    if (cudaMemcpyAsync(pr.data(), L.prob, sizeof(BwProb) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return 4;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return 4;      // the column counts shape the GEMMs
+  }
+  int64_t ns = 0;
+  for (int p = 0; p < batch; ++p) {
+    if (!g_Q_cat) pr[p].s = 0;
+    pr[p].g = ns;
+    ns += pr[p].n * pr[p].s;
+    cum[batch + 1 + p + 1] = ns;
+  }
+  size_t off = L.fixed;
+  L.G = reinterpret_cast<double*>(b + off);
+  off = al(off + (size_t)std::max<int64_t>(ns, 1) * 8);
+  L.P = reinterpret_cast<double*>(b + off);
+  off = al(off + (size_t)std::max<int64_t>(ns, 1) * 8);
+  L.W = reinterpret_cast<double*>(b + off);
+  off = al(off + (size_t)std::max<int64_t>(ns, 1) * 8);
+  if (off > ws_bytes) return 3;
+  cudaMemcpyAsync(L.prob, pr.data(), sizeof(BwProb) * batch, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.cum, cum.data(), sizeof(int64_t) * 2 * (batch + 1), cudaMemcpyHostToDevice, st);
+  const int64_t* cum_n = L.cum;
+  const int64_t* cum_ns = L.cum + batch + 1;
+  if (ns > 0) {
+    const unsigned gb = grid_cap((ns + 255) / 256, 8);
+    k_bwb_gather<<<gb, 256, 0, st>>>(L.prob, batch, cum_ns, ns, g_Q_cat, L.cols, L.G);
+    std::vector<HGemm> g;
+    for (int p = 0; p < batch; ++p) {           // P = Q^T G
+      if (pr[p].s == 0) continue;
+      HGemm h;
+      std::memset(&h, 0, sizeof(h));
+      h.M = (int)pr[p].n; h.N = pr[p].s; h.K = (int)pr[p].n;
+      h.a.mode = HOP_DENSE_T; h.a.p = Q_cat + pr[p].q; h.a.ld = pr[p].n;
+      h.b.mode = HOP_DENSE; h.b.p = L.G + pr[p].g; h.b.ld = pr[p].n;
+      h.C = L.P + pr[p].g; h.ldc = pr[p].n; h.alpha = 1.0;
+      g.push_back(h);
+    }
+    size_t toff = 0;
+    if (g.size() * sizeof(HGemm) + (g.size() + 1) * 8 + 1024 > kBwTab / 2) return 3;
+    launch_dense_gemms(g, L.tab, toff, st);
+    k_bwb_m<<<gb, 256, 0, st>>>(L.prob, batch, cum_ns, ns, L.P, lambda_cat, L.cols, L.G);   // M into G
+    for (HGemm& h : g) {                         // W = Q M: same shapes, same offsets
+      const int64_t go = h.C - L.P;
+      h.a.mode = HOP_DENSE;
+      h.b.p = L.G + go;
+      h.C = L.W + go;
+    }
+    launch_dense_gemms(g, L.tab, toff, st);
+  }
+  k_bwb_band<<<(unsigned)((vtot + 255) / 256), 256, 0, st>>>(L.prob, batch, cum_n, vtot, Q_cat, g_lambda_cat,
+                                                             L.W, L.cols, g_d_cat, g_e_cat);
   return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }

@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "tdc_ozaki.cuh"
 
@@ -593,10 +594,18 @@ void launch_s(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const
               const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t, int64_t ntiles, QBufs qb, DevWs w,
               cudaStream_t st) {
   using C = OzCfg<S>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    attr = true;
+  // the shared-memory opt-in is a per-device attribute of the kernel: set it once on
+  // every device that launches it
+  static std::mutex mu;
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+      cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
   }
   if (part == 0) {
     if (nb_sa) k_oz_slice_a<S><<<(unsigned)nb_sa, 256, 0, st>>>(jobs, ozj, njobs, cum_sa, w);

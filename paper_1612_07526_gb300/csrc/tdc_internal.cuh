@@ -177,6 +177,17 @@ __device__ __forceinline__ double warp_prod(double v) {
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
 // Counts HSS merges that fell back to the dense product (while profiling is on).
 void hss_fallbacks_add(int n);
+// While an object constructed with `on` = true lives, phase_mark records nothing on
+// the constructing thread (no CUDA events are created).
+struct ProfileSuspend {
+  explicit ProfileSuspend(bool on);
+  ~ProfileSuspend();
+  ProfileSuspend(const ProfileSuspend&) = delete;
+  ProfileSuspend& operator=(const ProfileSuspend&) = delete;
+
+ private:
+  bool prev_;
+};
 
 // Grid size for a grid-stride kernel: min(nb, SMs x per_sm), at least 1.
 unsigned grid_cap(int64_t nb, int per_sm);

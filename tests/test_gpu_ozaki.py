@@ -53,10 +53,12 @@ def test_merge_ozaki_vs_oracle_and_fp64(api, n1, n2, seed):
     assert err <= 1e-8
 
 
-@pytest.mark.parametrize("gen,n", [("toeplitz", 4096), ("uniform", 3000), ("normal", 2500), ("clement", 2049)])
+@pytest.mark.parametrize("gen,n", [("toeplitz", 4096), ("uniform", 3000), ("normal", 2500), ("clement", 2049),
+                                   ("sht", 3000)])
 def test_syev_ozaki(api, gen, n):
     d, e = {"toeplitz": lambda: W.toeplitz_121(n), "uniform": lambda: W.uniform_tridiag(n, 3),
-            "normal": lambda: W.normal_tridiag(n, 4), "clement": lambda: W.clement(n)}[gen]()
+            "normal": lambda: W.normal_tridiag(n, 4), "clement": lambda: W.clement(n),
+            "sht": lambda: W.sht(n)}[gen]()
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
     lam_o, q_o = api.syev_tridiag(dt, et, opts={"path": OZ})
     lam_f, q_f = api.syev_tridiag(dt, et, opts={"path": 0})

@@ -324,3 +324,48 @@ def test_backward_hellmann_feynman():
     gd, ge = backward.band_gradient(lam, q, g_lam=w)
     assert np.allclose(gd, (q * q) @ w, atol=1e-13)
     assert np.allclose(ge, 2 * (q[:-1] * q[1:]) @ w, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- metrics
+def test_tri_matmul_against_dense_product():
+    """T Q for T = tridiag(e, d, e) equals the dense product; a band offset by one row
+    or a transposed coupling would change entries of this non-symmetric Q."""
+    d, e = W.uniform_tridiag(9, 21)
+    q = W.rng(22).standard_normal((9, 4))
+    t = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.allclose(metrics.tri_matmul(d, e, q), t @ q, rtol=0, atol=1e-15)
+    d2, e2 = np.array([1.0, 2.0, 3.0]), np.array([10.0, 20.0])
+    q2 = np.array([[1.0], [0.0], [0.0]])               # first column of T: (1, 10, 0)
+    assert np.array_equal(metrics.tri_matmul(d2, e2, q2)[:, 0], [1.0, 10.0, 0.0])
+
+
+def test_scaled_residual_values():
+    """Zero for exact eigenpairs of a diagonal T; for a planted residual the value
+    ||R||_F / (n eps ||T||_1) computed by hand."""
+    d = np.array([3.0, -1.0, 2.0])
+    e = np.zeros(2)
+    lam = d.copy()
+    q = np.eye(3)
+    assert metrics.scaled_residual(d, e, lam, q) == 0.0
+    lam_bad = lam + np.array([0.0, 2.0 ** -40, 0.0])   # residual column (0, -2^-40, 0), exact
+    assert metrics.scaled_residual(d, e, lam_bad, q) == 2.0 ** -40 / (3 * EPS * 3.0)
+    assert metrics.tnorm([1.0, -2.0, 0.5], [4.0, -1.0]) == 7.0     # max row sum |e|+|d|+|e|
+
+
+def test_orthogonality_and_column_agreement_values():
+    q = np.linalg.qr(W.rng(23).standard_normal((6, 6)))[0]
+    assert metrics.orthogonality(q) <= 10 * EPS
+    q2 = q.copy()
+    q2[:, 1] *= 1.0 + 1e-9                             # ||q_1||^2 - 1 = 2e-9 + 1e-18
+    assert np.isclose(metrics.orthogonality(q2), 2e-9, rtol=1e-6)
+    lam = np.arange(6.0)
+    flipped = q * np.array([1, -1, 1, -1, 1, 1])[None, :]
+    err, mask = metrics.column_agreement(lam, q, flipped, 6.0)
+    assert err <= 1e-15 and mask.all()                 # signs are free
+    bent = q.copy()
+    bent[:, 2] += 1e-7 * q[:, 3]
+    err, _ = metrics.column_agreement(lam, q, bent, 6.0)
+    assert np.isclose(err, 1e-7, rtol=1e-6)
+    lam_close = np.array([0.0, 1.0, 1.0 + 1e-12, 3.0, 4.0, 5.0])
+    _, mask = metrics.column_agreement(lam_close, q, q, 6.0, min_relgap=1e-6)
+    assert list(mask) == [True, False, False, True, True, True]

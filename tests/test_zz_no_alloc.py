@@ -70,3 +70,32 @@ def test_noalloc_matches_workspace_entry_twice(lib):
         assert err <= 1e-7
         assert metrics.scaled_residual(d, e, la, qa) <= 10
         assert metrics.orthogonality(qa) <= 100 * n * EPS
+
+
+@pytest.mark.gpu
+def test_noalloc_call_takes_no_device_memory(lib):
+    """With its outputs allocated beforehand, a call changes the device's free memory by
+    nothing (a device allocation would take at least one 2 MiB page), and it records no
+    per-phase events even while the library's profiling is on."""
+    from paper_1612_07526_gb300 import _lib
+    n = 400
+    d, e = W.uniform_tridiag(n, 9)
+    dt = torch.tensor(d, device="cuda")
+    et = torch.tensor(e, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    q = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.tdc_syev_tridiag_noalloc(n, _vp(dt), _vp(et), _vp(lam), _vp(q), n, _vp(st), sp) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    lib.tdc_profile_begin()
+    assert lib.tdc_syev_tridiag_noalloc(n, _vp(dt), _vp(et), _vp(lam), _vp(q), n, _vp(st), sp) == 0
+    torch.cuda.synchronize()
+    prof = _lib.TdcProfile()
+    assert lib.tdc_profile_end(ctypes.byref(prof)) == 0
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert sum(prof.launches) == 0 and prof.calls == 0
+    assert int(st.item()) == 0
+    assert metrics.scaled_residual(d, e, lam.cpu().numpy(), q.cpu().numpy()) <= 10
