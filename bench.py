@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--path", default="fp64", choices=list(PATHS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--leaf", type=int, default=32)
+    ap.add_argument("--leaf", type=int, default=8,
+                    help="leaf order of the DC tree (8: fastest at n = 32768; the library default is 32)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the few-deflation and batched context measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the FP64 tile-shape autotuning")
@@ -226,6 +227,10 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
         out["split_operand_split_ms"] = p.ms[9]
         out["split_gemm_bf16_tflops"] = p.split_tensor_flops / (p.ms[8] * 1e-3) / 1e12
     out["phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES)}
+    if p.ms[10] > 0:                 # HSS: the sampling GEMMs' FP64 rate (exact flops 4 K^2 (r + p))
+        out["hss"] = {"sampling_flops": p.hss_sampling_flops,
+                      "sampling_fp64_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
+                      "regrowths": int(p.hss_regrowths), "dense_fallbacks": int(p.hss_fallbacks)}
     out["K_total"] = int(p.K_total)
     out["accuracy"] = sampled_accuracy(torch, d, e, lam, q)
     if exact is not None:           # closed-form eigenvalues: max |error| / (n eps ||T||)
@@ -318,7 +323,59 @@ def context_measurements(api, _lib, lib, torch):
                            "tile_shapes": ",".join(map(str, shapes))}
     del plan, q, lam
     torch.cuda.empty_cache()
+    ctx["backward_batched_64x4096"] = backward_measurement(api, _lib, lib, torch)
     return ctx
+
+
+def backward_measurement(api, _lib, lib, torch, batch=64, n=4096, m=64):
+    """The differentiable configuration: 64 problems of n = 4096 (d, e ~ N(0, 1)), loss
+    sum_i w_i lambda_i + ||Q[:, :64]^T G||_F^2 per problem.  Times the batched forward
+    (graph replay of the batched plan) and the batched backward to (d, e); the backward's
+    work is 2 products of n x n x 64 per problem (Q^T Qbar_S, then Q M_S: 4 n^2 64 flops)
+    plus the band sums of the lambda term (6 n^2 flops), on the FP64 pipe."""
+    import numpy as np
+    import workloads as W
+    sizes = np.full(batch, n, dtype=np.int64)
+    ds = [W.normal_tridiag(n, 500 + p)[0] for p in range(batch)]
+    es = [W.normal_tridiag(n, 500 + p)[1] for p in range(batch)]
+    plan = api.BatchedPlan(sizes, opts={"path": PATHS["fp64"]})
+    d_cat, e_cat = plan.pack(ds, es)
+    lam, q = plan.outputs()
+    plan.autotune(d_cat, e_cat, lam, q)
+    plan.capture(d_cat, e_cat, lam, q)
+    for _ in range(2):
+        plan.replay()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    plan.replay()
+    f1.record()
+    f1.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+    w = torch.tensor(np.concatenate([W.gaussian(n, 900 + p) for p in range(batch)]), device="cuda")
+    gq = torch.zeros_like(q)
+    for p in range(batch):
+        G = torch.tensor(W.gaussian((n, m), 1000 + p), device="cuda")
+        qp = q[p * n * n:(p + 1) * n * n].view(n, n).t()
+        gq[p * n * n:(p + 1) * n * n].view(n, n).t()[:, :m] = 2.0 * G @ (G.t() @ qp[:, :m])
+    api.syev_backward_batched(sizes, lam, q, w, gq, max_cols=m)
+    torch.cuda.synchronize()
+    reps = 3
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for _ in range(reps):
+        gd, ge = api.syev_backward_batched(sizes, lam, q, w, gq, max_cols=m)
+    b1.record()
+    b1.synchronize()
+    bw_ms = b0.elapsed_time(b1) / reps
+    flops = batch * (4.0 * n * n * m + 6.0 * n * n)
+    out = {"forward_ms": fwd_ms, "backward_ms": bw_ms, "problems": batch, "n": n, "loss_columns": m,
+           "backward_algorithmic_flops": flops,
+           "backward_fp64_tflops": flops / (bw_ms * 1e-3) / 1e12,
+           "note": "backward timed with its one stream synchronization (the column count) inside"}
+    del plan, q, lam, gq, d_cat, e_cat
+    torch.cuda.empty_cache()
+    return out
 
 
 def _cpulist(text):

@@ -23,7 +23,8 @@
  *    nothing launched); 3 = workspace too small; 4 = a CUDA error was reported at
  *    launch.  Conditions found on the device are OR-ed into *dev_status (a device
  *    int the call zeroes first): bit 0 (1) = a secular root hit the iteration cap,
- *    bit 1 (2) = non-finite input, bit 2 (4) = a leaf QL iteration hit its cap.
+ *    bit 1 (2) = non-finite input, bit 2 (4) = a leaf QL iteration hit its cap,
+ *    bit 3 (8) = a bounded device wait timed out.
  *    dev_status may be NULL (the status is then kept in the workspace).
  *  - No entry point aborts, throws, traps the device, or reads host memory from a
  *    kernel.
@@ -61,7 +62,21 @@ typedef struct tdc_opts {
                              /* 128x32, 64x16, 128x16                                   */
   int32_t secular_lanes;     /* lanes per secular root: 0 = chosen per tree level from  */
                              /* the level's root count (default), or 4, 8, 16, 32        */
+  int32_t eigvec;            /* how the eigenvectors of D + rho z z^T keep orthogonal    */
+                             /* (Section 1): TDC_EIGVEC_LOWNER (default) or             */
+                             /* TDC_EIGVEC_EXTENDED                                       */
+  int32_t hss_grow;          /* HSS: times r + p may be doubled when an ID rank reaches  */
+                             /* the sample count (adaptive sampling), 0..4 (default 1);  */
+                             /* a merge still saturated after that takes the dense       */
+                             /* FP64 product                                              */
 } tdc_opts;
+
+/* tdc_opts.eigvec: the Loewner-theorem z of Remark 1 (Gu and Eisenstat), or Sorensen and
+ * Tang's extended precision: each root is refined to double-double (tau + tau_lo, one
+ * Newton step on the secular function evaluated in double-double arithmetic), the
+ * original z is kept, and every difference d_j - lambda_i of the eigenvector
+ * (D - lambda_i)^{-1} z is formed in double-double before it is rounded. */
+enum tdc_eigvec { TDC_EIGVEC_LOWNER = 0, TDC_EIGVEC_EXTENDED = 1 };
 
 /* Fills *opts with the defaults listed above. */
 void tdc_default_opts(tdc_opts* opts);
@@ -159,7 +174,10 @@ int tdc_merge(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t 
  *              columns (j, k) become (c q_j + s q_k, -s q_j + c q_k)
  *   dbar, zbar [K]: the non-deflated values
  *   origin [K] (int32, index into dbar), tau [K]: the roots
- *   zhat [K]: the Loewner z;  sinv [K]: 1 / ||(D - lambda_i)^{-1} zhat||
+ *   zhat [K]: the Loewner z (the original z with TDC_EIGVEC_EXTENDED);
+ *   sinv [K]: 1 / ||(D - lambda_i)^{-1} zhat||
+ *   tau_lo [K]: with TDC_EIGVEC_EXTENDED, the low parts of the roots (tau + tau_lo);
+ *              not written otherwise
  * Returns as tdc_merge.
  */
 typedef struct tdc_merge_trace {
@@ -179,6 +197,7 @@ typedef struct tdc_merge_trace {
   double* tau;
   double* zhat;
   double* sinv;
+  double* tau_lo;
 } tdc_merge_trace;
 int tdc_merge_inspect(int64_t n1, int64_t n2, const double* D, const double* Q, int64_t ldq,
                       double beta, double* lambda, double* Q_out, int64_t ldqo, int64_t* K_out,
@@ -252,10 +271,14 @@ int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n_host, cons
  * 2 secular roots, 3 Loewner z + column norms, 4 eigenvalue placement,
  * 5 eigenvector product on the FP64 or HSS form (Eq. 6), 6 deflated-column copy,
  * 7 sign normalisation, 8 split-precision product (the tcgen05 GEMM alone),
- * 9 operand split of the split-precision product (digit slices of Q_sel and Qhat).
+ * 9 operand split of the split-precision product (digit slices of Q_sel and Qhat),
+ * and inside phase 5 for HSS merges: 10 sampling (Omega, Y = Qhat Omega1,
+ * Z = Qhat^T Omega2, the leaves' Phi and Theta), 11 compression (IDs, couplings B,
+ * the rank check; repeated when the sample grows), 12 HSS multiply (up-sweep,
+ * couplings, down-sweep, leaf blocks).
  * Not thread-safe; meant for benchmarks.
  */
-#define TDC_NPHASE 10
+#define TDC_NPHASE 13
 #define TDC_PROFILE_LEVELS 32
 typedef struct tdc_profile {
   double ms[TDC_NPHASE];           /* summed event time per phase                     */
@@ -274,7 +297,10 @@ typedef struct tdc_profile {
   double secular_flops;            /* 7 K x (secular-function evaluations) per merge:
                                       K terms of one division and three FMA each        */
   int64_t hss_fallbacks;           /* HSS merges whose ID ranks reached the sample count
-                                      (r + p) and that took the dense product instead   */
+                                      (r + p) even after the adaptive growths and that
+                                      took the dense product instead                      */
+  int64_t hss_regrowths;           /* HSS compressions repeated with a doubled sample  */
+  double hss_sampling_flops;       /* 4 K^2 (r + p) per HSS compression: Y and Z       */
   double level_fp64_min_bytes[TDC_PROFILE_LEVELS];   /* per tree level (leaves up): the
                                       product_min_bytes of its merges on the FP64 product */
   double level_fp64_flops[TDC_PROFILE_LEVELS];       /* the same for fp64_product_flops  */
@@ -388,6 +414,18 @@ int tdc_diag_reciprocal(const double* x, double* r, int64_t n, void* stream);
  * within a few units in the last place.  Arguments and returns as tdc_diag_reciprocal.
  */
 int tdc_diag_rsqrt(const double* x, double* r, int64_t n, void* stream);
+
+/*
+ * tdc_diag_wait_timeout -- diagnostic of the bounded device waits: runs the split-
+ * precision product's mbarrier wait (the one its producer, MMA and epilogue roles use)
+ * on a barrier that nothing arrives on, with a limit of limit_ns nanoseconds.  The
+ * wait gives up after the limit, ORs bit 3 (8, a timed-out wait) into *dev_status and
+ * writes 0 to *dev_out (1 if the wait had completed); the kernel then returns and the
+ * context stays usable.  limit_ns in [1000, 2e9] (the product's own limit is 2 s).
+ * dev_status, dev_out: device ints.  Asynchronous on `stream`.  Returns 0, -i for a
+ * bad argument i, or 4 for a launch error.
+ */
+int tdc_diag_wait_timeout(int64_t limit_ns, int* dev_status, int* dev_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -302,11 +302,14 @@ def merge(D: np.ndarray, Q: np.ndarray, n1: int, beta: float):
 
 
 def merge_hss(D: np.ndarray, Q: np.ndarray, n1: int, beta: float, leaf: int, rp: int, tol: float,
-              seed: int):
+              seed: int, grow: int = 0):
     """The merge of ``merge`` with Qhat replaced by its HSS approximation (Section 2.2):
     Qhat, in the order of the sorted non-deflated d, is compressed by Algorithm 1 with
     the Gaussian sampling matrices Omega1 = G(seed, 1), Omega2 = G(seed, 2)
-    (``hss.gaussian_matrix``), and Q_sel Qhat is formed by the HSS multiply."""
+    (``hss.gaussian_matrix``), and Q_sel Qhat is formed by the HSS multiply.  With
+    grow > 0 the sample is doubled up to `grow` times while an ID rank reaches it
+    (``hss.rand_hss_adaptive``); a compression still saturated after that is not used:
+    the merge keeps the exact product (info["hss_dense"] = True)."""
     from . import hss
     lam, u, info = merge(D, Q, n1, beta)
     kk = info["K"]
@@ -320,9 +323,9 @@ def merge_hss(D: np.ndarray, Q: np.ndarray, n1: int, beta: float, leaf: int, rp:
         cols[:, j] = c * cj + s * ck
         cols[:, k] = -s * cj + c * ck
     qsel = cols[:, info["kept"]]
-    om1 = hss.gaussian_matrix(seed, 1, kk, rp)
-    om2 = hss.gaussian_matrix(seed, 2, kk, rp)
-    root, nodes = hss.rand_hss(info["qhat"], om1, om2, leaf, tol)
+    root, nodes, rp_used, sat = hss.rand_hss_adaptive(info["qhat"], seed, rp, grow, leaf, tol)
+    if sat:
+        return lam, u, dict(info, hss_ranks=hss.hss_ranks(nodes), hss_rp=rp_used, hss_dense=True)
     u_nd = hss.hss_left_multiply(qsel, root, nodes)
     # place the non-deflated columns where ``merge`` put them
     fin = info["final_order"]
@@ -330,7 +333,7 @@ def merge_hss(D: np.ndarray, Q: np.ndarray, n1: int, beta: float, leaf: int, rp:
     pos = np.empty(n, dtype=np.int64)
     pos[fin] = np.arange(n)
     out[:, pos[:kk]] = u_nd
-    info = dict(info, hss_ranks=hss.hss_ranks(nodes))
+    info = dict(info, hss_ranks=hss.hss_ranks(nodes), hss_rp=rp_used, hss_dense=False)
     return lam, out, info
 
 

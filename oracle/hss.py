@@ -231,3 +231,36 @@ def hss_left_multiply(x: np.ndarray, root, nodes) -> np.ndarray:
 
 def hss_ranks(nodes):
     return [nd.U.shape[1] for nd in nodes if nd.U is not None]
+
+
+def saturated(nodes, rp: int) -> bool:
+    """True when some non-root node's row or column ID kept all rp sample columns while
+    its sample had more rows than that: the sampled range may then miss part of the
+    off-diagonal block, and the compression cannot be trusted at the tolerance."""
+    for nd in nodes:
+        if nd.parent is None or nd.U is None:
+            continue
+        if (nd.U.shape[1] >= rp and nd.U.shape[0] > rp) or (nd.V.shape[1] >= rp and nd.V.shape[0] > rp):
+            return True
+    return False
+
+
+def rand_hss_adaptive(a, seed: int, rp0: int, grow: int, leaf: int, tol: float):
+    """Algorithm 1 with the sample grown as the paper's adaptive sampling does
+    (Section 2.1): compress with r + p = rp0 Gaussian sample columns; while a node's ID
+    rank reaches the sample count, double it (at most `grow` times) and compress again
+    with the larger sample, whose first columns are the previous sample's (column c of
+    ``gaussian_matrix`` does not depend on the column count).  Returns
+    (root, nodes, rp used, still saturated)."""
+    a = np.asarray(a, dtype=np.float64)
+    k = a.shape[0]
+    rp = rp0
+    for g in range(grow + 1):
+        om1 = gaussian_matrix(seed, 1, k, rp)
+        om2 = gaussian_matrix(seed, 2, k, rp)
+        root, nodes = rand_hss(a, om1, om2, leaf, tol)
+        if not saturated(nodes, rp):
+            return root, nodes, rp, False
+        if g < grow:
+            rp *= 2
+    return root, nodes, rp, True

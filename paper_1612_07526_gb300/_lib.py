@@ -27,13 +27,19 @@ class TdcOpts(ctypes.Structure):
         ("max_secular_iter", ctypes.c_int32),
         ("tile_cfg", ctypes.c_int32),
         ("secular_lanes", ctypes.c_int32),
+        ("eigvec", ctypes.c_int32),
+        ("hss_grow", ctypes.c_int32),
     ]
+
+
+EIGVEC_LOWNER = 0
+EIGVEC_EXTENDED = 1
 
 
 class TdcProfile(ctypes.Structure):
     _fields_ = [
-        ("ms", ctypes.c_double * 10),
-        ("launches", ctypes.c_int64 * 10),
+        ("ms", ctypes.c_double * 13),
+        ("launches", ctypes.c_int64 * 13),
         ("product_flops", ctypes.c_double),
         ("product_min_bytes", ctypes.c_double),
         ("merges", ctypes.c_int64),
@@ -45,6 +51,8 @@ class TdcProfile(ctypes.Structure):
         ("defl_copy_bytes", ctypes.c_double),
         ("secular_flops", ctypes.c_double),
         ("hss_fallbacks", ctypes.c_int64),
+        ("hss_regrowths", ctypes.c_int64),
+        ("hss_sampling_flops", ctypes.c_double),
         ("level_fp64_min_bytes", ctypes.c_double * 32),
         ("level_fp64_flops", ctypes.c_double * 32),
     ]
@@ -54,11 +62,12 @@ class TdcMergeTrace(ctypes.Structure):
     """Device pointers receiving a merge's intermediate values (tdc_merge_inspect)."""
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "counts", "perm", "d_sorted", "z_sorted", "kept", "deflated", "rot_j", "rot_k", "rot_c", "rot_s",
-        "dbar", "zbar", "origin", "tau", "zhat", "sinv")]
+        "dbar", "zbar", "origin", "tau", "zhat", "sinv", "tau_lo")]
 
 
 PHASES = ["tear+leaves", "deflation", "secular", "lowner+norms", "placement", "product",
-          "deflated-copy", "sign", "split-product", "operand-split"]
+          "deflated-copy", "sign", "split-product", "operand-split", "hss-sampling", "hss-compression",
+          "hss-multiply"]
 
 _lib = None
 
@@ -103,6 +112,7 @@ SIGNATURES = [
     ("tdc_version", ctypes.c_char_p, []),
     ("tdc_diag_reciprocal", ctypes.c_int, [_P, _P, _I64, _P]),
     ("tdc_diag_rsqrt", ctypes.c_int, [_P, _P, _I64, _P]),
+    ("tdc_diag_wait_timeout", ctypes.c_int, [_I64, _P, _P, _P]),
 ]
 
 

@@ -166,7 +166,8 @@ def merge_inspect(D: torch.Tensor, Q: torch.Tensor, n1: int, beta: float, opts=N
     """tdc_merge plus the merge's intermediate values (tdc_merge_inspect).  Returns
     (lam, Q_out, trace) with trace a dict of host numpy arrays cut to their defined
     lengths: counts (K, nd, nrot, c1, c3, type-1 count), perm, d_sorted, z_sorted,
-    kept, deflated, rot_j, rot_k, rot_c, rot_s, dbar, zbar, origin, tau, zhat, sinv."""
+    kept, deflated, rot_j, rot_k, rot_c, rot_s, dbar, zbar, origin, tau, zhat, sinv,
+    tau_lo (zeros unless opts.eigvec is extended)."""
     lib = _lib.load()
     n = int(D.shape[0])
     assert Q.stride() == (1, n) and Q.shape == (n, n) and Q.dtype == torch.float64
@@ -195,7 +196,8 @@ def merge_inspect(D: torch.Tensor, Q: torch.Tensor, n1: int, beta: float, opts=N
     h = {k: v.cpu().numpy() for k, v in bufs.items()}
     K, nd, nrot = int(h["counts"][0]), int(h["counts"][1]), int(h["counts"][2])
     cut = {"perm": n, "d_sorted": n, "z_sorted": n, "kept": K, "deflated": nd, "rot_j": nrot, "rot_k": nrot,
-           "rot_c": nrot, "rot_s": nrot, "dbar": K, "zbar": K, "origin": K, "tau": K, "zhat": K, "sinv": K}
+           "rot_c": nrot, "rot_s": nrot, "dbar": K, "zbar": K, "origin": K, "tau": K, "zhat": K, "sinv": K,
+           "tau_lo": K}
     for k, m in cut.items():
         h[k] = h[k][:m]
     return lam, qo, h
@@ -366,6 +368,30 @@ def syev_backward(lam: torch.Tensor, q: torch.Tensor, g_lam=None, g_q=None, stre
                                        _vp(ge if n > 1 else None), None, _vp(ws), ws.numel(), None,
                                        _stream(stream))
     _check_rc(rc, "tdc_syev_tridiag_backward")
+    return gd, ge
+
+
+def syev_backward_batched(sizes, lam_cat: torch.Tensor, q_cat: torch.Tensor, g_lam_cat=None, g_q_cat=None,
+                          max_cols: int = -1, stream=None):
+    """(g_d_cat, g_e_cat) for a batch in the batched forward's dense packing
+    (tdc_syev_tridiag_backward_batched): lam_cat / g_lam_cat hold sum(n) values,
+    q_cat / g_q_cat the n_p x n_p column-major blocks back to back; g_e_cat holds
+    problem p's n_p - 1 entries at the same offset as its d (its last slot is zero)."""
+    lib = _lib.load()
+    sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+    b = len(sizes)
+    dev = lam_cat.device
+    tot = int(sizes.sum())
+    gd = torch.empty(tot, dtype=torch.float64, device=dev)
+    ge = torch.zeros(tot, dtype=torch.float64, device=dev)
+    sp = sizes.ctypes.data_as(ctypes.c_void_p)
+    nb = lib.tdc_backward_batched_workspace_bytes(b, sp, int(max_cols), None)
+    if nb == 0:
+        raise ValueError("invalid sizes")
+    ws = workspace(nb, dev, key="backward_batched")
+    rc = lib.tdc_syev_tridiag_backward_batched(b, sp, _vp(lam_cat), _vp(q_cat), _vp(g_lam_cat), _vp(g_q_cat),
+                                               _vp(gd), _vp(ge), None, _vp(ws), ws.numel(), None, _stream(stream))
+    _check_rc(rc, "tdc_syev_tridiag_backward_batched")
     return gd, ge
 
 

@@ -177,8 +177,11 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.zs = c.take<double>(N);
   w.dbar = c.take<double>(N);
   w.zbar = c.take<double>(N);
+  w.dbar32 = c.take<float>(N);
+  w.zbar32 = c.take<float>(N);
   w.zhat = c.take<double>(N);
   w.tau = c.take<double>(N);
+  w.taulo = c.take<double>(N);
   w.sinv = c.take<double>(N);
   w.cmax = c.take<double>(N);
   w.lamnd = c.take<double>(N);
@@ -241,7 +244,9 @@ static bool opts_valid(const tdc_opts& o) {
          o.max_secular_iter >= 1 && o.ozaki_slices >= 5 && o.ozaki_slices <= 7 && o.hss_leaf >= 16 &&
          o.hss_rp >= 8 && o.hss_tol > 0.0 &&
          (o.secular_lanes == 0 || o.secular_lanes == 4 || o.secular_lanes == 8 || o.secular_lanes == 16 ||
-          o.secular_lanes == 32);
+          o.secular_lanes == 32) &&
+         (o.eigvec == TDC_EIGVEC_LOWNER || o.eigvec == TDC_EIGVEC_EXTENDED) && o.hss_grow >= 0 &&
+         o.hss_grow <= 4;
 }
 
 template <class T>
@@ -260,9 +265,11 @@ static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
   return v;
 }
 
-static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const tdc_opts& o,
+static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L_in, const tdc_opts& o,
                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
                     bool sign_norm, double* qa_for_sign, cudaStream_t st) {
+  Layout L = L_in;
+  L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   // leaves of one element and n < 2^31 give at most 31 merge levels
   static_assert(kMaxLevels >= 32, "level table too small");
   cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
@@ -277,11 +284,6 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
     const int nj = (int)lv.jobs.size();
     if (nj == 0) continue;
     const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
-    launch_merge_level((int)li, jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
-                       lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
-                       o.max_secular_iter, o.secular_lanes, st);
-    const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
-    if (prc) return prc;
     bool any_root = false, any_fin = false;
     int64_t maxm = 0;
     for (const MergeJob& J : lv.jobs) {
@@ -289,6 +291,11 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L, const td
       any_fin |= J.fin != 0;
       maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
     }
+    launch_merge_level((int)li, jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
+                       lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
+                       o.max_secular_iter, o.secular_lanes, merge_cta_threads(maxm), st);
+    const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
+    if (prc) return prc;
     // deflated columns move only in a problem's top merge; below, the slot table keeps them in place
     if (any_fin)
       launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
@@ -377,11 +384,12 @@ struct ProfState {
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<ProfRec> recs;
-  cudaEvent_t open_ev = nullptr;
+  cudaEvent_t open_ev[TDC_NPHASE] = {};   // per phase: the HSS phases nest inside phase 5
   int64_t launches[TDC_NPHASE] = {};
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   double secular_flops = 0.0;
-  int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0;
+  int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0, hss_regrowths = 0;
+  double hss_sampling_flops = 0.0;
   double lvl_bytes[TDC_PROFILE_LEVELS] = {}, lvl_flops[TDC_PROFILE_LEVELS] = {};
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
@@ -398,6 +406,12 @@ ProfileSuspend::~ProfileSuspend() { t_prof_suspended = prev_; }
 void hss_fallbacks_add(int n) {
   if (g_prof.on && !t_prof_suspended) g_prof.hss_fallbacks += n;
 }
+void hss_regrowths_add(int n) {
+  if (g_prof.on && !t_prof_suspended) g_prof.hss_regrowths += n;
+}
+void hss_sampling_flops_add(double f) {
+  if (g_prof.on && !t_prof_suspended) g_prof.hss_sampling_flops += f;
+}
 
 static cudaEvent_t prof_event() {
   if (g_prof.used == g_prof.pool.size()) {
@@ -410,13 +424,15 @@ static cudaEvent_t prof_event() {
 
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
   if (!g_prof.on || t_prof_suspended) return;
+  if (phase < 0 || phase >= TDC_NPHASE) return;
   if (begin) {
-    g_prof.open_ev = prof_event();
-    cudaEventRecord(g_prof.open_ev, st);
-  } else {
+    g_prof.open_ev[phase] = prof_event();
+    cudaEventRecord(g_prof.open_ev[phase], st);
+  } else if (g_prof.open_ev[phase]) {
     cudaEvent_t b = prof_event();
     cudaEventRecord(b, st);
-    g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev, b});
+    g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev[phase], b});
+    g_prof.open_ev[phase] = nullptr;
     g_prof.launches[phase] += nlaunch;
   }
 }
@@ -566,11 +582,12 @@ static void copy_trace(const tdc_merge_trace& t, const DevWs& w, int64_t n, cuda
   trace_copy(t.tau, w.tau, n, st);
   trace_copy(t.zhat, w.zhat, n, st);
   trace_copy(t.sinv, w.sinv, n, st);
+  if (w.ext) trace_copy(t.tau_lo, w.taulo, n, st);
 }
 
 }  // namespace tdc
 
-static_assert(sizeof(tdc_opts) == 48, "tdc_opts layout is part of the ABI");
+static_assert(sizeof(tdc_opts) == 56, "tdc_opts layout is part of the ABI");
 
 using namespace tdc;
 
@@ -588,6 +605,7 @@ void tdc_default_opts(tdc_opts* o) {
   o->ozaki_slices = 6;
   o->max_secular_iter = 64;
   o->tile_cfg = -1;
+  o->hss_grow = 1;
 }
 
 const char* tdc_version(void) { return "tdc 0.1 (sm_103a)"; }
@@ -771,19 +789,20 @@ static int merge_core(int64_t n1, int64_t n2, const double* D, const double* Q, 
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   cudaMemcpyAsync(lambda, D, n * 8, cudaMemcpyDeviceToDevice, st);
   QBufs qb{Q_out, L.pool, Q};
+  L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   const LevelPlan& lv = P.levels[0];
   const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
   cudaMemsetAsync(L.w.lroots, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(L.w.scal, 0, sizeof(MergeScalars), st);
   launch_merge_level(0, jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
-                     qb, L.w, o.max_secular_iter, o.secular_lanes, st);
+                     qb, L.w, o.max_secular_iter, o.secular_lanes, merge_cta_threads(n), st);
   const int prc = launch_product(pp, 0, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
   if (prc) return prc;
   launch_defl_copy(jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
                    lv.ccols.back(), n, qb, L.w, false, st);
   if (K_out) launch_copy_k(L.w.scal, K_out, st);
-  if (tr) copy_trace(*tr, L.w, n, st);
+  if (tr) copy_trace(*tr, L.w, n, st);       // L.w.ext set above
   prof_account(P, pp, L.w.scal, st);
   return launch_status();
 }
@@ -881,7 +900,9 @@ void tdc_profile_begin(void) {
   for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
   g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
-  g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = 0;
+  g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = g_prof.hss_regrowths = 0;
+  g_prof.hss_sampling_flops = 0.0;
+  for (int i = 0; i < TDC_NPHASE; ++i) g_prof.open_ev[i] = nullptr;
   for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) g_prof.lvl_bytes[l] = g_prof.lvl_flops[l] = 0.0;
 }
 
@@ -906,6 +927,8 @@ int tdc_profile_end(tdc_profile* out) {
   out->defl_copy_bytes = g_prof.copy_bytes;
   out->secular_flops = g_prof.secular_flops;
   out->hss_fallbacks = g_prof.hss_fallbacks;
+  out->hss_regrowths = g_prof.hss_regrowths;
+  out->hss_sampling_flops = g_prof.hss_sampling_flops;
   for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) {
     out->level_fp64_min_bytes[l] = g_prof.lvl_bytes[l];
     out->level_fp64_flops[l] = g_prof.lvl_flops[l];

@@ -452,8 +452,8 @@ struct HssLayout {
 
 // The arena layout for K non-deflated columns of an order-m merge (base may be null
 // to size it).
-void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts& o) {
-  const int rp = o.hss_rp, hl = std::max(o.hss_leaf, 2);
+void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts& o, int rp) {
+  const int hl = std::max(o.hss_leaf, 2);
   const int rmax = std::max(hl, 2 * rp);
   Bump b{base};
   L.dK = b.take<int>(1);
@@ -546,9 +546,12 @@ void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, siz
   launch_gemms(g, dev_tab, tab_off, q, xc, st);
 }
 
+// The largest sample an HSS merge may grow to: r + p doubled hss_grow times.
+int hss_rp_max(const tdc_opts& o) { return o.hss_rp << std::max(0, std::min(o.hss_grow, 4)); }
+
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o) {
   HssLayout L;
-  hss_layout(L, nullptr, (int)m, (int)m, o);
+  hss_layout(L, nullptr, (int)m, (int)m, o, hss_rp_max(o));   // every layout fits in the largest
   return L.bytes + 4096;
 }
 
@@ -565,6 +568,8 @@ __global__ void k_hss_saturated(const HssNodeDev* __restrict__ nd, int nn, int r
   }
 }
 
+void k_hss_saturated_zero(int* flag, cudaStream_t st) { cudaMemsetAsync(flag, 0, sizeof(int), st); }
+
 int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, size_t arena_bytes,
                   const tdc_opts& o, cudaStream_t st) {
   // K is needed on the host to shape the HSS tree
@@ -574,125 +579,154 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   cudaMemcpyAsync(&K, dK, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
   if (K == 0) return 0;
-  const int rp = o.hss_rp, m = hJ.n1 + hJ.n2;
-  const int rmax = std::max(std::max(o.hss_leaf, 2), 2 * rp);
-  HssLayout L;
-  hss_layout(L, arena, K, m, o);
-  if (L.bytes > arena_bytes) return 3;
-  const int nn = (int)L.tree.size();
-  const auto& tree = L.tree;
-  auto& nd = L.nd;
+  const int m = hJ.n1 + hJ.n2;
   const int64_t o_v = hJ.v_off;
   QhatSrc q{w.wptr + o_v, w.sinv + o_v};
-  HssCols xc = L.xc;
-  xc.n1 = hJ.n1;
   double* const* outp = w.outptr + o_v;     // output column of each kept eigenpair
-  cudaMemcpyAsync(L.dnodes, nd.data(), nn * sizeof(HssNodeDev), cudaMemcpyHostToDevice, st);
+  HssLayout L;
+  HssCols xc{};
+  int nn = 0, maxlev = 0, rp = o.hss_rp, rmax = 0;
   size_t toff = 0;
-  unsigned char* tab = L.tab;
+  unsigned char* tab = nullptr;
+  std::vector<std::vector<int>> byl;
+  // Algorithm 1 with r + p = rp sample columns, then the check of the ID ranks against
+  // the sample count.  Returns 0, kHssSaturated, 3 or 4.
+  auto compress = [&]() -> int {
+    rmax = std::max(std::max(o.hss_leaf, 2), 2 * rp);
+    hss_layout(L, arena, K, m, o, rp);
+    if (L.bytes > arena_bytes) return 3;
+    nn = (int)L.tree.size();
+    const auto& tree = L.tree;
+    auto& nd = L.nd;
+    xc = L.xc;
+    xc.n1 = hJ.n1;
+    cudaMemcpyAsync(L.dnodes, nd.data(), nn * sizeof(HssNodeDev), cudaMemcpyHostToDevice, st);
+    toff = 0;
+    tab = L.tab;
 
-  // ---- sampling: Omega, Y = Qhat Omega1, Z = Qhat^T Omega2
-  const uint64_t seed = 0x5EEDull + (uint64_t)hJ.mid;
-  k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om1, K, rp, seed, 1);
-  k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om2, K, rp, seed, 2);
-  k_hss_cols<<<grid_cap(K / 256 + 1, 4), 256, 0, st>>>(hJ, w, xc);
-  {
-    std::vector<HGemm> g(2, gemm0());
-    g[0].M = K; g[0].N = rp; g[0].K = K;
-    g[0].a.mode = HOP_QHAT;
-    g[0].b.mode = HOP_DENSE; g[0].b.p = L.om1; g[0].b.ld = K;
-    g[0].C = L.Y; g[0].ldc = K;
-    g[1] = g[0];
-    g[1].a.mode = HOP_QHAT_T;
-    g[1].b.p = L.om2;
-    g[1].C = L.Z;
-    launch_gemms(g, tab, toff, q, xc, st);
-  }
-  // ---- leaves: Phi = Y(t) - D Omega1(t), Theta = Z(t) - D^T Omega2(t), in place
-  int maxlev = 0;
-  for (int i = 0; i < nn; ++i) maxlev = std::max(maxlev, tree[i].level);
-  std::vector<std::vector<int>> byl(maxlev + 1);
-  for (int i = 0; i < nn; ++i) byl[tree[i].level].push_back(i);
-  if (nn > 1) {
-    std::vector<HGemm> g;
-    for (int i = 0; i < nn; ++i) {
-      if (!nd[i].leaf) continue;
-      const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
-      HGemm a = gemm0();
-      a.M = sz; a.N = rp; a.K = sz;
-      a.a.mode = HOP_QHAT; a.a.r0 = lo; a.a.c0 = lo;
-      a.b.mode = HOP_DENSE; a.b.p = L.om1; a.b.ld = K; a.b.r0 = lo;
-      a.C = L.Y + lo; a.ldc = K; a.alpha = -1.0; a.beta = 1.0;
-      g.push_back(a);
-      HGemm b = a;
-      b.a.mode = HOP_QHAT_T;
-      b.b.p = L.om2;
-      b.C = L.Z + lo;
-      g.push_back(b);
+    // ---- sampling: Omega, Y = Qhat Omega1, Z = Qhat^T Omega2 (column c of Omega does
+    // not depend on rp, so a grown sample extends the previous one)
+    phase_mark(10, true, 0, st);
+    hss_sampling_flops_add(4.0 * (double)K * (double)K * (double)rp);
+    const uint64_t seed = 0x5EEDull + (uint64_t)hJ.mid;
+    k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om1, K, rp, seed, 1);
+    k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om2, K, rp, seed, 2);
+    k_hss_cols<<<grid_cap(K / 256 + 1, 4), 256, 0, st>>>(hJ, w, xc);
+    {
+      std::vector<HGemm> g(2, gemm0());
+      g[0].M = K; g[0].N = rp; g[0].K = K;
+      g[0].a.mode = HOP_QHAT;
+      g[0].b.mode = HOP_DENSE; g[0].b.p = L.om1; g[0].b.ld = K;
+      g[0].C = L.Y; g[0].ldc = K;
+      g[1] = g[0];
+      g[1].a.mode = HOP_QHAT_T;
+      g[1].b.p = L.om2;
+      g[1].C = L.Z;
+      launch_gemms(g, tab, toff, q, xc, st);
     }
-    launch_gemms(g, tab, toff, q, xc, st);
-  }
-  // ---- interpolative decompositions, leaves to root
-  const size_t id_smem = (size_t)(rmax + rp) * 8 + (size_t)rmax * 4 + 64;
-  int* lp = L.lists;
-  for (int lev = maxlev; lev >= 1; --lev) {
-    std::vector<int> parents, all;
-    for (int i : byl[lev]) {
-      all.push_back(i);
-      if (!nd[i].leaf) parents.push_back(i);
+    // ---- leaves: Phi = Y(t) - D Omega1(t), Theta = Z(t) - D^T Omega2(t), in place
+    maxlev = 0;
+    for (int i = 0; i < nn; ++i) maxlev = std::max(maxlev, tree[i].level);
+    byl.assign(maxlev + 1, {});
+    for (int i = 0; i < nn; ++i) byl[tree[i].level].push_back(i);
+    if (nn > 1) {
+      std::vector<HGemm> g;
+      for (int i = 0; i < nn; ++i) {
+        if (!nd[i].leaf) continue;
+        const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
+        HGemm a = gemm0();
+        a.M = sz; a.N = rp; a.K = sz;
+        a.a.mode = HOP_QHAT; a.a.r0 = lo; a.a.c0 = lo;
+        a.b.mode = HOP_DENSE; a.b.p = L.om1; a.b.ld = K; a.b.r0 = lo;
+        a.C = L.Y + lo; a.ldc = K; a.alpha = -1.0; a.beta = 1.0;
+        g.push_back(a);
+        HGemm b = a;
+        b.a.mode = HOP_QHAT_T;
+        b.b.p = L.om2;
+        b.C = L.Z + lo;
+        g.push_back(b);
+      }
+      launch_gemms(g, tab, toff, q, xc, st);
     }
-    if (!parents.empty()) {
-      cudaMemcpyAsync(lp, parents.data(), parents.size() * 4, cudaMemcpyHostToDevice, st);
-      k_hss_parent<<<(unsigned)parents.size(), 256, 0, st>>>(L.dnodes, lp, rp, q);
-      lp += parents.size();
+    phase_mark(10, false, 5, st);
+    phase_mark(11, true, 0, st);
+    // ---- interpolative decompositions, leaves to root
+    const size_t id_smem = (size_t)(rmax + rp) * 8 + (size_t)rmax * 4 + 64;
+    int* lp = L.lists;
+    for (int lev = maxlev; lev >= 1; --lev) {
+      std::vector<int> parents, all;
+      for (int i : byl[lev]) {
+        all.push_back(i);
+        if (!nd[i].leaf) parents.push_back(i);
+      }
+      if (!parents.empty()) {
+        cudaMemcpyAsync(lp, parents.data(), parents.size() * 4, cudaMemcpyHostToDevice, st);
+        k_hss_parent<<<(unsigned)parents.size(), 256, 0, st>>>(L.dnodes, lp, rp, q);
+        lp += parents.size();
+      }
+      std::vector<HIdJob> ids;
+      for (int i : all) {
+        HIdJob u;
+        std::memset(&u, 0, sizeof(u));
+        u.phi = nd[i].phi;
+        u.ld = nd[i].ldphi;
+        u.rows = nd[i].leaf ? tree[i].hi - tree[i].lo : 0;
+        u.rows_dev = nd[i].leaf ? nullptr : nd[i].rows_u;
+        u.rows_max = rmax;
+        u.U = nd[i].U;
+        u.rank_out = nd[i].kU;
+        u.skel_local = nd[i].Iloc;
+        u.scratch = L.idscratch + (size_t)(2 * i) * rp * rmax;
+        ids.push_back(u);
+        HIdJob v = u;
+        v.phi = nd[i].theta;
+        v.rows_dev = nd[i].leaf ? nullptr : nd[i].rows_v;
+        v.U = nd[i].V;
+        v.rank_out = nd[i].kV;
+        v.skel_local = nd[i].Jloc;
+        v.scratch = L.idscratch + (size_t)(2 * i + 1) * rp * rmax;
+        ids.push_back(v);
+      }
+      toff = (toff + 255) & ~size_t(255);
+      if (toff + ids.size() * sizeof(HIdJob) > kTabBytes) return 3;
+      HIdJob* did = reinterpret_cast<HIdJob*>(tab + toff);
+      cudaMemcpyAsync(did, ids.data(), ids.size() * sizeof(HIdJob), cudaMemcpyHostToDevice, st);
+      toff += ids.size() * sizeof(HIdJob);
+      k_hss_id<<<(unsigned)ids.size(), 256, id_smem, st>>>(did, o.hss_tol, rp);
+      cudaMemcpyAsync(lp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st);
+      k_hss_hat<<<(unsigned)all.size(), 256, 0, st>>>(L.dnodes, lp, rp, L.om1, L.om2, K);
+      lp += all.size();
     }
-    std::vector<HIdJob> ids;
-    for (int i : all) {
-      HIdJob u;
-      std::memset(&u, 0, sizeof(u));
-      u.phi = nd[i].phi;
-      u.ld = nd[i].ldphi;
-      u.rows = nd[i].leaf ? tree[i].hi - tree[i].lo : 0;
-      u.rows_dev = nd[i].leaf ? nullptr : nd[i].rows_u;
-      u.rows_max = rmax;
-      u.U = nd[i].U;
-      u.rank_out = nd[i].kU;
-      u.skel_local = nd[i].Iloc;
-      u.scratch = L.idscratch + (size_t)(2 * i) * rp * rmax;
-      ids.push_back(u);
-      HIdJob v = u;
-      v.phi = nd[i].theta;
-      v.rows_dev = nd[i].leaf ? nullptr : nd[i].rows_v;
-      v.U = nd[i].V;
-      v.rank_out = nd[i].kV;
-      v.skel_local = nd[i].Jloc;
-      v.scratch = L.idscratch + (size_t)(2 * i + 1) * rp * rmax;
-      ids.push_back(v);
+    const int root = L.root;
+    if (!nd[root].leaf) {                       // root: couplings of its children only
+      cudaMemcpyAsync(lp, &root, 4, cudaMemcpyHostToDevice, st);
+      k_hss_parent<<<1, 256, 0, st>>>(L.dnodes, lp, rp, q);
+      lp += 1;
     }
-    toff = (toff + 255) & ~size_t(255);
-    if (toff + ids.size() * sizeof(HIdJob) > kTabBytes) return 3;
-    HIdJob* did = reinterpret_cast<HIdJob*>(tab + toff);
-    cudaMemcpyAsync(did, ids.data(), ids.size() * sizeof(HIdJob), cudaMemcpyHostToDevice, st);
-    toff += ids.size() * sizeof(HIdJob);
-    k_hss_id<<<(unsigned)ids.size(), 256, id_smem, st>>>(did, o.hss_tol, rp);
-    cudaMemcpyAsync(lp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st);
-    k_hss_hat<<<(unsigned)all.size(), 256, 0, st>>>(L.dnodes, lp, rp, L.om1, L.om2, K);
-    lp += all.size();
+    if (nn > 1) k_hss_saturated_zero(L.dK, st);
+    if (nn > 1) k_hss_saturated<<<1, 256, 0, st>>>(L.dnodes, nn, rp, L.dK);
+    phase_mark(11, false, 3 * maxlev + 2, st);
+    if (nn > 1) {                               // ranks that reached the sample count
+      int sat = 0;
+      cudaMemcpyAsync(&sat, L.dK, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
+      if (sat) return kHssSaturated;
+    }
+    return 0;
+  };
+  // Adaptive sampling (Section 2.1): while an ID rank reaches the sample count, double
+  // r + p and compress again, at most hss_grow times; then the caller's dense product.
+  for (int g = 0;; ++g) {
+    const int rc = compress();
+    if (rc == 0) break;
+    if (rc != kHssSaturated) return rc;
+    if (g >= std::max(0, std::min(o.hss_grow, 4))) return kHssSaturated;
+    hss_regrowths_add(1);
+    rp *= 2;
   }
-  const int root = L.root;
-  if (!nd[root].leaf) {                       // root: couplings of its children only
-    cudaMemcpyAsync(lp, &root, 4, cudaMemcpyHostToDevice, st);
-    k_hss_parent<<<1, 256, 0, st>>>(L.dnodes, lp, rp, q);
-    lp += 1;
-  }
-  if (nn > 1) {                               // ranks that hit the sample count: dense product instead
-    cudaMemsetAsync(L.dK, 0, sizeof(int), st);
-    k_hss_saturated<<<1, 256, 0, st>>>(L.dnodes, nn, rp, L.dK);
-    int sat = 0;
-    cudaMemcpyAsync(&sat, L.dK, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
-    if (sat) return kHssSaturated;
-  }
+  const auto& tree = L.tree;
+  auto& nd = L.nd;
+  phase_mark(12, true, 0, st);
 
   // ---- multiply: Out = X Qhat_hss, X = Q_sel (m rows, K kept columns)
   for (int lev = maxlev; lev >= 1; --lev) {   // up-sweep: G = X(:, t) U, G_p = [G_1 G_2] U_p
@@ -765,6 +799,7 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     launch_gemms(g1, tab, toff, q, xc, st);
     launch_gemms(g2, tab, toff, q, xc, st);
   }
+  phase_mark(12, false, 4 * maxlev + 2, st);
   return toff > kTabBytes ? 3 : 0;
 }
 

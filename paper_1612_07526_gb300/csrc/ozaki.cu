@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kThreads = 320;       // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
 constexpr int kEpiWarps = 8;        // two per TMEM lane quadrant, each owning 32 of a level's 64 columns
-constexpr long long kWaitNs = 10LL * 1000 * 1000 * 1000;   // bounded mbarrier waits (10 s)
+constexpr long long kWaitNs = 2LL * 1000 * 1000 * 1000;    // bounded mbarrier waits (2 s)
 
 __host__ __device__ constexpr int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -110,16 +110,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase with the given parity; gives up after kWaitNs or when another
-// role has aborted, setting the abort flag and the status bit.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+// Waits for the phase with the given parity; gives up after limit_ns (kWaitNs by
+// default) or when another role has aborted, setting the abort flag and the status bit.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                          long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = global_ns();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 255) == 255) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs) {
+      if (global_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicOr(err, ST_WAIT);
         return false;
@@ -702,3 +703,30 @@ int oz_slice_pairs(int slices) {
 }
 
 }  // namespace tdc
+
+namespace tdc {
+namespace {
+// The product kernel's bounded wait, on an mbarrier that nothing arrives on: after
+// limit_ns it sets the abort flag and ST_WAIT in *err and returns (no copy or MMA is
+// in flight, no tensor memory is held).  out[0] = 1 if the wait ended by itself.
+__global__ void k_diag_wait(long long limit_ns, int* err, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) out[0] = mbar_wait(smem_u32(&bar), 0u, &abort_flag, err, limit_ns) ? 1 : 0;
+}
+}  // namespace
+}  // namespace tdc
+
+extern "C" int tdc_diag_wait_timeout(int64_t limit_ns, int* dev_status, int* dev_out, void* stream) {
+  if (limit_ns < 1000 || limit_ns > tdc::kWaitNs) return -1;
+  if (!dev_status) return -2;
+  if (!dev_out) return -3;
+  tdc::k_diag_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>((long long)limit_ns, dev_status, dev_out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}

@@ -76,7 +76,9 @@ struct MergeScalars {
 struct DevWs {
   double *ds, *zs;            // sorted d and z (updated by rotations)
   double *dbar, *zbar;        // non-deflated (K) values
+  float *dbar32, *zbar32;     // their FP32 copies (the secular solver's FP32 phase)
   double *zhat, *tau, *sinv, *cmax;
+  double *taulo;              // extended-precision eigenvectors: the roots' low parts (tau + taulo)
   double *lamnd;              // non-deflated eigenvalues d_org + tau
   double *dv;                 // deflated eigenvalues (sorted-position order)
   double *skey;               // 2n scratch keys for the fallback sort
@@ -101,6 +103,7 @@ struct DevWs {
   uint8_t *lroti;             // leaf QL: row index i of each rotation (rows i, i+1)
   int32_t *lrotn;             // leaf QL: rotations recorded, or -1: redo the leaf serially
   int *status;                // per problem
+  int32_t ext;                // 1: extended-precision eigenvectors (tdc_opts.eigvec), else Loewner z
 };
 
 constexpr int kMaxLevels = 64;   // merge levels of one plan (log2 of the largest n / leaf, plus one)
@@ -177,6 +180,10 @@ __device__ __forceinline__ double warp_prod(double v) {
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
 // Counts HSS merges that fell back to the dense product (while profiling is on).
 void hss_fallbacks_add(int n);
+// Counts HSS compressions repeated with a doubled sample (while profiling is on).
+void hss_regrowths_add(int n);
+// Adds the sampling flops of one HSS compression (while profiling is on).
+void hss_sampling_flops_add(double f);
 // While an object constructed with `on` = true lives, phase_mark records nothing on
 // the constructing thread (no CUDA events are created).
 struct ProfileSuspend {
@@ -200,10 +207,12 @@ void launch_leaves(const LeafJob* jobs, int njobs, const double* dmod, const dou
 // Rank-one merges of one tree level (`lev`, 0 = the lowest; w.lroots and w.scal zeroed
 // before the first level of a solve).  cum_cols: the prefix of the merges' orders.
 // sec_lanes: lanes per secular root, 0 = chosen from the level's root count.
+// cta: threads of the one-CTA-per-merge kernels, merge_cta_threads(largest merge).
+int merge_cta_threads(int64_t maxm);
 void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                         const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
-                        int max_iter, int sec_lanes, cudaStream_t st);
+                        int max_iter, int sec_lanes, int cta, cudaStream_t st);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
 // 32x32, 128x32, 64x16, 128x16.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
 // tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.

@@ -43,7 +43,8 @@ def test_opts_struct_layout(lib):
     from paper_1612_07526_gb300 import _lib
     o = _lib.default_opts()
     assert o.leaf == 32 and o.path == 0 and o.hss_tol == 1e-12 and o.max_secular_iter == 64
-    assert ctypes.sizeof(_lib.TdcOpts) == 48
+    assert ctypes.sizeof(_lib.TdcOpts) == 56
+    assert o.eigvec == 0 and o.hss_grow == 1
 
 
 def test_host_side_argument_checks(lib):

@@ -113,3 +113,75 @@ def test_backward_config_size_finite_differences(api):
     scale = max(np.abs(rd).max(), np.abs(re).max())
     assert np.max(np.abs(grad[:n] - rd)) <= 1e-9 * scale
     assert np.max(np.abs(grad[n:] - re)) <= 1e-9 * scale
+
+
+def _batched_case(api, sizes, m, seed):
+    """A batch solved by the batched plan, the configuration's loss per problem
+    (w_p, G_p with m columns, m <= n_p), its (lambda_bar, Qbar) in the batch packing."""
+    ds, es, ws, Gs = [], [], [], []
+    for k, n in enumerate(sizes):
+        d, e = W.normal_tridiag(int(n), seed + 10 * k)
+        ds.append(d)
+        es.append(e)
+        ws.append(W.gaussian(int(n), seed + 10 * k + 1))
+        Gs.append(W.gaussian((int(n), min(m, int(n))), seed + 10 * k + 2))
+    lam, q, sz, qoff = api.syev_tridiag_batched(ds, es)
+    gl_cat = torch.tensor(np.concatenate(ws), device="cuda")
+    gq_cat = torch.zeros_like(q)
+    for p, n in enumerate(sizes):
+        qp = api.batched_block(q, sz, qoff, p)
+        Gp = torch.tensor(Gs[p], device="cuda")
+        mm = Gp.shape[1]
+        blk = gq_cat[int(qoff[p]):int(qoff[p]) + int(n) * int(n)].view(int(n), int(n)).t()
+        blk[:, :mm] = 2.0 * Gp @ (Gp.t() @ qp[:, :mm])
+    return ds, es, ws, Gs, lam, q, sz, qoff, gl_cat, gq_cat
+
+
+@pytest.mark.parametrize("sizes,m", [([1, 2, 33, 200, 64, 300, 513], 16), ([512] * 4, 64)])
+def test_backward_batched_matches_single_and_reference(api, sizes, m):
+    """The batched backward equals the single-problem entry bit for bit (same kernels,
+    same summation order per problem) and the dense FP64 reference gradient."""
+    ds, es, ws, Gs, lam, q, sz, qoff, gl_cat, gq_cat = _batched_case(api, sizes, m, 80)
+    gd, ge = api.syev_backward_batched(sz, lam, q, gl_cat, gq_cat, max_cols=m)
+    off = 0
+    for p, n in enumerate(sizes):
+        n = int(n)
+        lam_p = lam[off:off + n]
+        q_p = api.batched_block(q, sz, qoff, p)
+        gq_p = gq_cat[int(qoff[p]):int(qoff[p]) + n * n].view(n, n).t()
+        gd1, ge1 = api.syev_backward(lam_p.contiguous(), q_p, gl_cat[off:off + n].contiguous(), gq_p)
+        assert torch.equal(gd[off:off + n], gd1)
+        assert torch.equal(ge[off:off + n - 1], ge1)
+        lam_n, q_n = lam_p.cpu().numpy(), q_p.cpu().numpy()
+        rd, re = backward.band_gradient(lam_n, q_n, ws[p], gq_p.cpu().numpy())
+        scale = max(np.abs(rd).max(), np.abs(re).max() if n > 1 else 0.0)
+        assert np.max(np.abs(gd[off:off + n].cpu().numpy() - rd)) <= 1e-9 * scale
+        if n > 1:
+            assert np.max(np.abs(ge[off:off + n - 1].cpu().numpy() - re)) <= 1e-9 * scale
+        off += n
+
+
+def test_backward_batched_lambda_only_and_workspace_limit(api):
+    """Qbar absent: the Hellmann-Feynman gradient per problem; a workspace sized for
+    fewer nonzero columns than Qbar has is reported (3), not overrun."""
+    import ctypes
+    from paper_1612_07526_gb300 import _lib
+    sizes = [40, 100, 7]
+    ds, es, ws, Gs, lam, q, sz, qoff, gl_cat, gq_cat = _batched_case(api, sizes, 8, 90)
+    gd, ge = api.syev_backward_batched(sz, lam, q, gl_cat, None)
+    off = 0
+    for p, n in enumerate(sizes):
+        qn = api.batched_block(q, sz, qoff, p).cpu().numpy()
+        assert np.allclose(gd[off:off + n].cpu().numpy(), (qn * qn) @ ws[p], atol=1e-12, rtol=0)
+        assert np.allclose(ge[off:off + n - 1].cpu().numpy(), 2 * (qn[:-1] * qn[1:]) @ ws[p], atol=1e-12, rtol=0)
+        off += n
+    lib = _lib.load()
+    szc = np.ascontiguousarray(sz, dtype=np.int64)
+    sp = szc.ctypes.data_as(ctypes.c_void_p)
+    nb = lib.tdc_backward_batched_workspace_bytes(len(sizes), sp, 2, None)      # room for 2 columns each
+    wsb = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out = torch.empty(int(szc.sum()), dtype=torch.float64, device="cuda")
+    rc = lib.tdc_syev_tridiag_backward_batched(len(sizes), sp, api._vp(lam), api._vp(q), api._vp(gl_cat),
+                                               api._vp(gq_cat), api._vp(out), api._vp(out.clone()), None,
+                                               api._vp(wsb), nb, None, api._stream(None))
+    assert rc == 3

@@ -129,15 +129,15 @@ def _profiled(api, fn):
 
 
 def test_hss_saturated_ranks_take_dense_product(api):
-    """With r + p = 8 samples the ID ranks of tridiag(1,2,1)'s Cauchy-like Qhat blocks
-    reach the sample count, so every HSS merge (the 15 merges of order >= 2 x 128) takes
-    the dense FP64 product instead: the solve equals the FP64 path bit for bit.  With
-    the default 128 samples no merge falls back."""
+    """With r + p = 8 samples and no growth allowed the ID ranks of tridiag(1,2,1)'s
+    Cauchy-like Qhat blocks reach the sample count, so every HSS merge (the 15 merges of
+    order >= 2 x 128) takes the dense FP64 product instead: the solve equals the FP64
+    path bit for bit.  With the default 128 samples no merge falls back."""
     n = 3000
     d, e = W.toeplitz_121(n)
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
     (lam_h, q_h), p = _profiled(api, lambda: api.syev_tridiag(
-        dt, et, opts={"path": 2, "hss_rp": 8, "hss_leaf": 128, "tile_cfg": 2}))
+        dt, et, opts={"path": 2, "hss_rp": 8, "hss_leaf": 128, "tile_cfg": 2, "hss_grow": 0}))
     assert p.hss_fallbacks == 15
     lam_f, q_f = api.syev_tridiag(dt, et, opts={"path": 0, "tile_cfg": 2})
     assert torch.equal(lam_h, lam_f) and torch.equal(q_h, q_f)
@@ -179,3 +179,49 @@ def test_syev_auto_dispatch(api, gen, n, kt):
     sel = np.nonzero(gap >= 1e-3 * nrm)[0]
     dots = np.abs(np.sum(q[:, sel] * q_f.cpu().numpy()[:, sel], axis=0))
     assert np.all(1.0 - dots <= ((2 * b + 20 * n * EPS) * nrm / gap[sel]) ** 2 + 1e-13)
+
+
+
+def test_merge_hss_adaptive_growth(api):
+    """Adaptive sampling: from r + p = 8 the sample is doubled while an ID rank reaches
+    it (8 -> 16 -> 32 -> 64 here), and the merge equals the oracle's adaptive HSS merge
+    (same sampling columns) within the bound of the sample it ended with."""
+    n1, n2 = 600, 600
+    D, Q, beta = W.merge_problem(n1, n2, 5)
+    n = n1 + n2
+    lam_h, u_h, info = dc.merge_hss(D, Q, n1, beta, leaf=128, rp=8, tol=TOL, seed=0x5EED, grow=3)
+    assert not info["hss_dense"] and info["hss_rp"] == 64
+    lam_d, u_d, _ = dc.merge(D, Q, n1, beta)
+    opts = {"path": HSS, "hss_leaf": 128, "hss_rp": 8, "hss_tol": TOL, "hss_grow": 3}
+    (lam, qo, K), p = _profiled(api, lambda: api.merge(torch.tensor(D, device="cuda"), _fortran(Q), n1, beta,
+                                                       opts=opts))
+    assert p.hss_regrowths == 3 and p.hss_fallbacks == 0
+    qo = qo.cpu().numpy()
+    b = merge_bound(K, 128, 64)
+    assert np.linalg.norm(qo - u_h, 2) <= 2 * b + 100 * n * EPS
+    assert np.linalg.norm(qo - u_d, 2) <= b + 100 * n * EPS
+    assert np.max(np.abs(qo.T @ qo - np.eye(n))) <= 2 * b + 100 * n * EPS
+    # the grown sample extends the 64-column one: the same compression as r + p = 64
+    lam64, q64, _ = api.merge(torch.tensor(D, device="cuda"), _fortran(Q), n1, beta,
+                              opts={"path": HSS, "hss_leaf": 128, "hss_rp": 64, "hss_tol": TOL, "hss_grow": 0})
+    assert np.array_equal(q64.cpu().numpy(), qo)
+
+
+def test_syev_hss_adaptive_growth(api):
+    """A full HSS solve that starts every compression at r + p = 8: the samples grow
+    until the ranks fit, no merge falls back to the dense product, and the solve meets
+    the HSS contract of the largest sample it may reach."""
+    n = 3000
+    d, e = W.toeplitz_121(n)
+    dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
+    (lam_t, q_t), p = _profiled(api, lambda: api.syev_tridiag(
+        dt, et, opts={"path": HSS, "hss_rp": 8, "hss_leaf": 128, "hss_grow": 4}))
+    assert p.hss_regrowths >= 15 and p.hss_fallbacks == 0
+    lam, q = lam_t.cpu().numpy(), q_t.cpu().numpy()
+    nrm = metrics.tnorm(d, e)
+    lref, _ = sturm.closed_form_121(n)
+    assert np.max(np.abs(lam - lref)) <= 10 * n * EPS * nrm
+    b = syev_bound(n, 128, 8 << 4, lambda m: m >= 2 * 128)
+    assert metrics.orthogonality(q) <= 2 * b + 100 * n * EPS
+    r = metrics.tri_matmul(d, e, q) - q * lam[None, :]
+    assert np.linalg.norm(r) <= (2 * b * np.sqrt(n) + 10 * n * EPS) * nrm

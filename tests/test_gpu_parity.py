@@ -294,3 +294,21 @@ def test_full_size_32768(api, gen):
     del q_t
     torch.cuda.empty_cache()
 
+
+
+def test_bounded_wait_times_out_with_status(api):
+    """The split-precision product's bounded mbarrier wait, on a barrier nothing arrives
+    on, with a 2 ms limit: it gives up, reports status bit 8 and returns; the context
+    stays usable (a solve right after is correct)."""
+    from paper_1612_07526_gb300 import _lib
+    lib = _lib.load()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    rc = lib.tdc_diag_wait_timeout(2_000_000, api._vp(st), api._vp(out), api._stream(None))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) & 8 and int(out.item()) == 0
+    assert lib.tdc_diag_wait_timeout(10, api._vp(st), api._vp(out), api._stream(None)) == -1
+    d, e = W.uniform_tridiag(120, 4)
+    lam, q = _solve(api, d, e)
+    assert metrics.scaled_residual(d, e, lam, q) <= 10

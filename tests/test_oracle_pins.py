@@ -369,3 +369,77 @@ def test_orthogonality_and_column_agreement_values():
     lam_close = np.array([0.0, 1.0, 1.0 + 1e-12, 3.0, 4.0, 5.0])
     _, mask = metrics.column_agreement(lam_close, q, q, 6.0, min_relgap=1e-6)
     assert list(mask) == [True, False, False, True, True, True]
+
+
+# --------------------------------------------------------------------------- extended precision
+def test_extended_roots_against_exact_characteristic_polynomial():
+    """The exact roots (rational bisection) against the eigenvalues of D + rho z z^T
+    taken by sympy from its characteristic polynomial with rational entries, to 60
+    digits: tau differs from the polynomial's root by less than 2^-100 |tau|."""
+    sympy = pytest.importorskip("sympy")
+    from oracle import extended
+    g = W.rng(30)
+    for k in (3, 5, 6):
+        d = np.sort(g.uniform(-1, 1, k))
+        z = g.standard_normal(k)
+        z /= np.linalg.norm(z)
+        rho = 0.75
+        org, tau = dc.secular_roots(d, z, rho)
+        hi, lo, ex = extended.exact_roots(d, z, rho, org, tau)
+        ds = [sympy.Rational(float(x)) for x in d]
+        zs = [sympy.Rational(float(x)) for x in z]
+        a = sympy.diag(*ds) + sympy.Rational(0.75) * sympy.Matrix(zs) * sympy.Matrix(zs).T
+        lam = sympy.symbols("lam")
+        roots = sorted(sympy.Poly(a.charpoly(lam).as_expr(), lam).nroots(n=60, maxsteps=200))
+        for i in range(k):
+            t_ref = roots[i] - ds[int(org[i])]
+            t_ex = sympy.Rational(ex[i].numerator, ex[i].denominator)
+            assert abs(t_ex - t_ref) <= abs(t_ref) * sympy.Rational(1, 2 ** 100)
+            assert abs(hi[i] + lo[i] - float(t_ref)) <= 4 * np.spacing(abs(float(t_ref)))
+
+
+def test_extended_vectors_orthonormal_and_reconstruct():
+    """Eigenvectors from exact roots and the original z: orthonormal to a few units of
+    eps and D + rho z z^T = U Lambda U^T, also for clustered poles and graded z."""
+    from oracle import extended
+    g = W.rng(31)
+    for case in range(3):
+        k = 24
+        d = np.sort(g.uniform(-1, 1, k))
+        if case >= 1:
+            d[5] = d[4] + 1e-10
+            d[13] = d[12] + 3e-12
+            d = np.sort(d)
+        z = g.standard_normal(k) * (10.0 ** g.uniform(-4, 0, k) if case == 2 else 1.0)
+        z /= np.linalg.norm(z)
+        rho = 1.3
+        df = dc.deflate(d, z, rho)
+        d2, z2 = df["d"][df["kept"]], df["z"][df["kept"]]
+        org, tau = dc.secular_roots(d2, z2, rho)
+        hi, lo, ex = extended.exact_roots(d2, z2, rho, org, tau)
+        u = extended.extended_vectors(d2, z2, org, ex)
+        kk = len(d2)
+        assert np.max(np.abs(u.T @ u - np.eye(kk))) <= 4 * kk * EPS
+        lam = d2[org] + hi
+        a = np.diag(d2) + rho * np.outer(z2, z2)
+        assert np.linalg.norm(u @ np.diag(lam) @ u.T - a) <= 10 * kk * EPS * np.linalg.norm(a)
+
+
+def test_extended_merge_against_dense_merge():
+    """The extended-precision merge gives the same eigenpairs as the Loewner merge
+    (eigenvectors where the gaps allow) and satisfies the merge contract."""
+    from oracle import extended
+    D, Q, beta = W.merge_problem(30, 26, 32)
+    lam, u, info = extended.merge_extended(D, Q, 30, beta)
+    lam_l, u_l, _ = dc.merge(D, Q, 30, beta)
+    n = len(D)
+    assert np.array_equal(lam, lam_l)
+    a = Q @ np.diag(D) @ Q.T
+    v = np.zeros(n)
+    v[29] = 1.0
+    v[30] = np.sign(beta)
+    a += abs(beta) * np.outer(v, v)
+    assert np.linalg.norm(a @ u - u * lam) <= 10 * n * EPS * np.linalg.norm(a)
+    assert np.max(np.abs(u.T @ u - np.eye(n))) <= 100 * n * EPS
+    err, _ = metrics.column_agreement(lam_l, u_l, u, np.abs(a).sum(1).max(), min_relgap=1e-6)
+    assert err <= 1e-12
