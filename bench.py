@@ -726,6 +726,7 @@ def main():
     # per tree level (leaves up), per step: the FP64 product's algorithmic bytes and flops
     lvl_bytes = [prof.level_fp64_min_bytes[i] / args.steps for i in range(32)]
     lvl_flops = [prof.level_fp64_flops[i] / args.steps for i in range(32)]
+    lvl_ms = [prof.level_fp64_product_ms[i] / args.steps for i in range(32)]
     nlev = max([i + 1 for i in range(32) if lvl_bytes[i] > 0] + [0])
     gemm_launches = prof.launches[5] / 2 / args.steps          # k_gemm_sched + k_gemm_fp64 per level
     for c in cands:
@@ -756,7 +757,10 @@ def main():
         "config": workload_config(args),
         "run": {"tile_shapes": ("autotuned per level: " + ",".join(map(str, shapes))) if shapes else "size rule",
                 "step": step_kind, "direct_call_ms": direct_ms},
-        "fp64_product_levels": {"min_bytes_per_step": lvl_bytes[:nlev], "flops_per_step": lvl_flops[:nlev]},
+        "fp64_product_levels": {"min_bytes_per_step": lvl_bytes[:nlev], "flops_per_step": lvl_flops[:nlev],
+                                "ms_per_step": [round(x, 4) for x in lvl_ms[:nlev]],
+                                "fp64_tflops": [round(f / (t * 1e-3) / 1e12, 4) if t > 0 else None
+                                                for f, t in zip(lvl_flops[:nlev], lvl_ms[:nlev])]},
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,

@@ -58,8 +58,8 @@ typedef struct tdc_opts {
                              /* FP64-level accuracy for 34 instead of 26 slice products)  */
   int32_t max_secular_iter;  /* iteration cap per secular root (default 64)             */
   int32_t tile_cfg;          /* FP64 product tile shape: -1 = autotuned (else a size    */
-                             /* rule), 0..7 = 128x128, 128x64, 64x64, 64x32, 32x32,    */
-                             /* 128x32, 64x16, 128x16                                   */
+                             /* rule), 0..11 = 128x128, 128x64, 64x64, 64x32, 32x32,   */
+                             /* 128x32, 64x16, 128x16, 16x16, 16x32, 16x64, 32x16       */
   int32_t secular_lanes;     /* lanes per secular root: 0 = chosen per tree level from  */
                              /* the level's root count (default), or 4, 8, 16, 32        */
   int32_t eigvec;            /* how the eigenvectors of D + rho z z^T keep orthogonal    */
@@ -304,6 +304,8 @@ typedef struct tdc_profile {
   double level_fp64_min_bytes[TDC_PROFILE_LEVELS];   /* per tree level (leaves up): the
                                       product_min_bytes of its merges on the FP64 product */
   double level_fp64_flops[TDC_PROFILE_LEVELS];       /* the same for fp64_product_flops  */
+  double level_fp64_product_ms[TDC_PROFILE_LEVELS];  /* event time of each level's FP64
+                                                        product (tile count + GEMM)        */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);
@@ -369,7 +371,7 @@ int tdc_batched_plan_execute_host(const tdc_batched_plan* plan, const double* d_
                                   void* stream);
 
 /*
- * Autotuning of the FP64 product's tile shape per DC tree level (the eight shapes of
+ * Autotuning of the FP64 product's tile shape per DC tree level (the twelve shapes of
  * tdc_opts.tile_cfg).  Every FP64 product sums each output element over k in the
  * same order whatever the shape, so the shape changes speed, never results.
  *
@@ -397,6 +399,10 @@ int tdc_read_status(const int* dev_status, void* stream);
 
 /* Library version string. */
 const char* tdc_version(void);
+
+/* sizeof of the ABI's structs, for bindings to check their layouts: which = 0 tdc_opts,
+ * 1 tdc_profile, 2 tdc_merge_trace; 0 for any other value. */
+size_t tdc_struct_bytes(int which);
 
 /*
  * tdc_diag_reciprocal -- diagnostic: r[i] = the reciprocal of x[i] as the secular

@@ -55,6 +55,7 @@ class TdcProfile(ctypes.Structure):
         ("hss_sampling_flops", ctypes.c_double),
         ("level_fp64_min_bytes", ctypes.c_double * 32),
         ("level_fp64_flops", ctypes.c_double * 32),
+        ("level_fp64_product_ms", ctypes.c_double * 32),
     ]
 
 
@@ -110,6 +111,7 @@ SIGNATURES = [
     ("tdc_profile_begin", None, []),
     ("tdc_profile_end", ctypes.c_int, [ctypes.POINTER(TdcProfile)]),
     ("tdc_version", ctypes.c_char_p, []),
+    ("tdc_struct_bytes", ctypes.c_size_t, [ctypes.c_int]),
     ("tdc_diag_reciprocal", ctypes.c_int, [_P, _P, _I64, _P]),
     ("tdc_diag_rsqrt", ctypes.c_int, [_P, _P, _I64, _P]),
     ("tdc_diag_wait_timeout", ctypes.c_int, [_I64, _P, _P, _P]),
@@ -117,7 +119,8 @@ SIGNATURES = [
 
 
 # FP64 product tile shapes (rows, columns) by tdc_opts.tile_cfg index
-TILE_SHAPES = [(128, 128), (128, 64), (64, 64), (64, 32), (32, 32), (128, 32), (64, 16), (128, 16)]
+TILE_SHAPES = [(128, 128), (128, 64), (64, 64), (64, 32), (32, 32), (128, 32), (64, 16), (128, 16),
+               (16, 16), (16, 32), (16, 64), (32, 16)]
 
 
 def load(path: str = LIB_PATH):

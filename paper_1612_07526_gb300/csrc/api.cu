@@ -384,7 +384,9 @@ struct ProfState {
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<ProfRec> recs;
-  cudaEvent_t open_ev[TDC_NPHASE] = {};   // per phase: the HSS phases nest inside phase 5
+  // open event per phase (the HSS phases nest inside phase 5), then per tree level of
+  // the FP64 product (phase ids kLevelMark + level)
+  cudaEvent_t open_ev[TDC_NPHASE + TDC_PROFILE_LEVELS] = {};
   int64_t launches[TDC_NPHASE] = {};
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   double secular_flops = 0.0;
@@ -424,16 +426,18 @@ static cudaEvent_t prof_event() {
 
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
   if (!g_prof.on || t_prof_suspended) return;
-  if (phase < 0 || phase >= TDC_NPHASE) return;
+  int slot = phase;
+  if (phase >= kLevelMark && phase < kLevelMark + TDC_PROFILE_LEVELS) slot = TDC_NPHASE + (phase - kLevelMark);
+  else if (phase < 0 || phase >= TDC_NPHASE) return;
   if (begin) {
-    g_prof.open_ev[phase] = prof_event();
-    cudaEventRecord(g_prof.open_ev[phase], st);
-  } else if (g_prof.open_ev[phase]) {
+    g_prof.open_ev[slot] = prof_event();
+    cudaEventRecord(g_prof.open_ev[slot], st);
+  } else if (g_prof.open_ev[slot]) {
     cudaEvent_t b = prof_event();
     cudaEventRecord(b, st);
-    g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev[phase], b});
-    g_prof.open_ev[phase] = nullptr;
-    g_prof.launches[phase] += nlaunch;
+    g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev[slot], b});
+    g_prof.open_ev[slot] = nullptr;
+    if (phase < TDC_NPHASE) g_prof.launches[phase] += nlaunch;
   }
 }
 
@@ -608,7 +612,16 @@ void tdc_default_opts(tdc_opts* o) {
   o->hss_grow = 1;
 }
 
-const char* tdc_version(void) { return "tdc 0.1 (sm_103a)"; }
+const char* tdc_version(void) { return "tdc 0.2 (sm_103a)"; }
+
+size_t tdc_struct_bytes(int which) {
+  switch (which) {
+    case 0: return sizeof(tdc_opts);
+    case 1: return sizeof(tdc_profile);
+    case 2: return sizeof(tdc_merge_trace);
+    default: return 0;
+  }
+}
 
 size_t tdc_workspace_bytes(int64_t n, const tdc_opts* opts) {
   const tdc_opts o = resolve_opts(opts);
@@ -902,7 +915,7 @@ void tdc_profile_begin(void) {
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
   g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = g_prof.hss_regrowths = 0;
   g_prof.hss_sampling_flops = 0.0;
-  for (int i = 0; i < TDC_NPHASE; ++i) g_prof.open_ev[i] = nullptr;
+  for (int i = 0; i < TDC_NPHASE + TDC_PROFILE_LEVELS; ++i) g_prof.open_ev[i] = nullptr;
   for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) g_prof.lvl_bytes[l] = g_prof.lvl_flops[l] = 0.0;
 }
 
@@ -913,7 +926,8 @@ int tdc_profile_end(tdc_profile* out) {
   for (const ProfRec& r : g_prof.recs) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.a, r.b);
-    out->ms[r.ph] += ms;
+    if (r.ph >= kLevelMark) out->level_fp64_product_ms[r.ph - kLevelMark] += ms;
+    else out->ms[r.ph] += ms;
   }
   for (int i = 0; i < TDC_NPHASE; ++i) out->launches[i] = g_prof.launches[i];
   out->product_flops = g_prof.flops;

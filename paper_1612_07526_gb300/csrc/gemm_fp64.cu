@@ -9,7 +9,7 @@
 // use the first two groups and rows of T2 the last two, so the zero blocks of
 // diag(Q1, Q2) are never multiplied.
 //
-// Tile shapes BM x BN x 8 (BM in {32, 64, 128}, BN in {16, 32, 64, 128}), 256 threads
+// Tile shapes BM x BN x 8 (BM in {16, 32, 64, 128}, BN in {16, 32, 64, 128}), 256 threads
 // in a 16 x 16 grid,
 // (BM/16) x (BN/16) FP64 accumulators per thread, double-buffered shared memory;
 // the next slab of Qhat is loaded while the current one is consumed.  Every
@@ -30,8 +30,8 @@ constexpr int BK = 8, NT = 256;
 struct Shape {
   int bm, bn;
 };
-constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32},
-                                        {32, 32},   {128, 32}, {64, 16}, {128, 16}};
+constexpr Shape kShapes[kGemmShapes] = {{128, 128}, {128, 64}, {64, 64}, {64, 32}, {32, 32}, {128, 32},
+                                        {64, 16},   {128, 16}, {16, 16}, {16, 32}, {16, 64}, {32, 16}};
 
 template <int BM, int BN>
 struct GemmSmem {
@@ -47,7 +47,8 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
                                           int njobs, const int64_t* __restrict__ cum, QBufs qb, DevWs w) {
   constexpr int TM = BM / 16, TN = BN / 16;         // accumulators per thread
   constexpr int NB = BN * BK;                       // Qhat entries per slab (128 for BN = 16)
-  constexpr int LA = BM * BK / NT, LB = NB >= NT ? NB / NT : 1;  // loads / generated entries per thread
+  constexpr int NA = BM * BK;                       // Q_sel entries per slab (128 for BM = 16)
+  constexpr int LA = NA >= NT ? NA / NT : 1, LB = NB >= NT ? NB / NT : 1;  // loads / generated entries per thread
   auto& As = sm.As;
   auto& Bs = sm.Bs;
   const int jb = find_job(cum, njobs, vb);
@@ -83,14 +84,16 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
   }
   __syncthreads();
 
-  // loader mapping: thread t covers LA consecutive rows (LB columns) of one k row
-  const int la_k = (tid * LA) / BM, la_r = (tid * LA) % BM;
+  // loader mapping: thread t covers LA consecutive rows (LB columns) of one k row;
+  // narrow slabs use their first NA (NB) threads
+  const bool la_on = tid * LA < NA;
+  const int la_k = la_on ? (tid * LA) / BM : 0, la_r = la_on ? (tid * LA) % BM : 0;
   const bool lb_on = tid * LB < NB;                // narrow slabs: the first NB threads
   const int lb_k = lb_on ? (tid * LB) / BN : 0, lb_c = lb_on ? (tid * LB) % BN : 0;
   double ra[LA], rb[LB];
   auto load_a = [&](int k0) {
     const int k = k0 + la_k;
-    if (k < kend) {
+    if (la_on && k < kend) {
       const double* col = colptr[k];
       const int lo = max(w.klo[o + k], r0), hi = min(w.khi[o + k], rend);   // rows that can be nonzero
 #pragma unroll
@@ -118,8 +121,9 @@ __device__ __forceinline__ void gemm_tile(int64_t vb, GemmSmem<BM, BN>& sm, cons
     }
   };
   auto store = [&](int stg) {
+    if (la_on)
 #pragma unroll
-    for (int u = 0; u < LA; ++u) As[stg][la_k][la_r + u] = ra[u];
+      for (int u = 0; u < LA; ++u) As[stg][la_k][la_r + u] = ra[u];
     if (lb_on)
 #pragma unroll
       for (int u = 0; u < LB; ++u) Bs[stg][lb_k][lb_c + u] = rb[u];
@@ -250,7 +254,11 @@ void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_til
     case 4: launch_shape<32, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 5: launch_shape<128, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
     case 6: launch_shape<64, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
-    default: launch_shape<128, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 7: launch_shape<128, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 8: launch_shape<16, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 9: launch_shape<16, 32>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    case 10: launch_shape<16, 64>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
+    default: launch_shape<32, 16>(jobs, njobs, cum_tiles, bound, qb, w, st); break;
   }
 }
 

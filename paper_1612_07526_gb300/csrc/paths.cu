@@ -19,10 +19,11 @@ std::mutex g_tune_mu;
 std::map<std::vector<int64_t>, std::vector<int>> g_tune;
 LevelTimer* g_timer = nullptr;
 
-// Size rule: tile rows no larger than the merge halves, 32 columns for the smallest
-// merges, else 64 (K is known only on the device).
+// Size rule: tile rows no larger than the merge halves, 16 or 32 columns for the
+// smallest merges, else 64 (K is known only on the device).
 int default_shape(int64_t maxm) {
-  if (maxm <= 64) return 4;
+  if (maxm <= 32) return 8;
+  if (maxm <= 64) return 11;
   if (maxm <= 128) return 3;
   return 1;
 }
@@ -184,7 +185,9 @@ int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vect
   } else {
     const bool timed = g_timer && l >= 0 && l < (int)g_timer->a.size();
     if (timed) cudaEventRecord(g_timer->a[l], st);
+    phase_mark(kLevelMark + l, true, 0, st);
     launch_gemm_fp64(L ? L->gemm_cfg : 1, jobs, (int)hjobs.size(), cum_tiles, L ? L->gemm_bound : 0, qb, w, st);
+    phase_mark(kLevelMark + l, false, 0, st);
     if (timed) {
       cudaEventRecord(g_timer->b[l], st);
       g_timer->used[l] = true;

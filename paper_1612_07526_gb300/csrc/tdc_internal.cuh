@@ -178,6 +178,8 @@ __device__ __forceinline__ double warp_prod(double v) {
 // Profiling hook (defined in api.cu): brackets a phase with CUDA events when the
 // per-phase timing of tdc_profile_begin() is on; a no-op otherwise.
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
+// Phase id of tree level l's FP64 product (kLevelMark + l): timed per level.
+constexpr int kLevelMark = 100;
 // Counts HSS merges that fell back to the dense product (while profiling is on).
 void hss_fallbacks_add(int n);
 // Counts HSS compressions repeated with a doubled sample (while profiling is on).
@@ -214,7 +216,8 @@ void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t*
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
                         int max_iter, int sec_lanes, int cta, cudaStream_t st);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
-// 32x32, 128x32, 64x16, 128x16.  cum_tiles (njobs + 1 entries of device memory) is rewritten with the
+// 32x32, 128x32, 64x16, 128x16, 16x16, 16x32, 16x64, 32x16 (rows x columns).
+// cum_tiles (njobs + 1 entries of device memory) is rewritten with the
 // tile prefix of the level's actual K; `bound` is the host's upper bound on tiles.
 void launch_gemm_fp64(int cfg, const MergeJob* jobs, int njobs, int64_t* cum_tiles, int64_t bound,
                       QBufs qb, DevWs w, cudaStream_t st);
@@ -230,6 +233,6 @@ void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_w8, in
                       bool any_root, cudaStream_t st);
 
 
-constexpr int kGemmShapes = 8;
+constexpr int kGemmShapes = 12;
 
 }  // namespace tdc

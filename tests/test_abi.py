@@ -100,3 +100,15 @@ def test_workspace_sizes(lib):
     sizes = (ctypes.c_int64 * 3)(100, 2000, 32)
     b = lib.tdc_batched_workspace_bytes(3, sizes, ctypes.byref(o))
     assert b >= 3 * 8 * (100 ** 2 + 2000 ** 2 + 32 ** 2)
+
+
+def test_struct_layouts_match_the_library():
+    """The ctypes mirrors of tdc_opts, tdc_profile and tdc_merge_trace have the sizes the
+    library was compiled with."""
+    import ctypes
+    from paper_1612_07526_gb300 import _lib
+    lib = _lib.load()
+    assert lib.tdc_struct_bytes(0) == ctypes.sizeof(_lib.TdcOpts)
+    assert lib.tdc_struct_bytes(1) == ctypes.sizeof(_lib.TdcProfile)
+    assert lib.tdc_struct_bytes(2) == ctypes.sizeof(_lib.TdcMergeTrace)
+    assert lib.tdc_struct_bytes(3) == 0

@@ -1,5 +1,5 @@
 """FP64 product tile shapes and their autotuner.  Every shape sums each output
-element over k in the same order, so all eight shapes must give bit-identical
+element over k in the same order, so all twelve shapes must give bit-identical
 eigenpairs; the solve itself is checked against the oracle's pins (Sturm-count
 bisection for the eigenvalues, residual and orthogonality bounds).  The autotuner
 must return valid shapes and leave the results unchanged, for single solves and
@@ -58,7 +58,7 @@ def test_autotune_single(api):
     lam0, q0 = api.syev_tridiag(dt, et, opts={"tile_cfg": 2})
     shapes = api.autotune(dt, et)
     assert len(shapes) == 6                       # merge levels 64 .. 2048 above leaves of 32
-    assert all(0 <= s < 8 for s in shapes)
+    assert all(0 <= s < len(api._lib.TILE_SHAPES) for s in shapes)
     lam1, q1 = api.syev_tridiag(dt, et)          # tile_cfg = -1: the tuned shapes
     assert torch.equal(lam0, lam1) and torch.equal(q0, q1)
 
@@ -71,7 +71,7 @@ def test_autotune_batched_plan_graph(api):
     d_cat, e_cat = plan.pack(ds, es)
     lam, q = plan.outputs()
     shapes = plan.autotune(d_cat, e_cat, lam, q)
-    assert len(shapes) >= 1 and all(0 <= s < 8 for s in shapes)
+    assert len(shapes) >= 1 and all(0 <= s < len(api._lib.TILE_SHAPES) for s in shapes)
     lam_b, q_b, _, _ = api.syev_tridiag_batched(ds, es, opts={"tile_cfg": 0})
     lam2, q2 = plan.outputs()
     plan.capture(d_cat, e_cat, lam2, q2)
