@@ -150,7 +150,7 @@ def time_oracle(gen, n, leaf):
     return time.perf_counter() - t0
 
 
-def cpu_oracle_fit(gen, n_full, leaf, sizes=(4096, 8192)):
+def cpu_oracle_fit(gen, n_full, leaf, sizes=(8192, 16384)):
     """A bounded CPU-oracle sample: solves of orders `sizes` (seed 0, same distribution),
     timed once each (the CPU has no warm-up effect), and the time at n_full from the
     power law t = c n^p through the two largest points (p fitted, not assumed)."""
@@ -411,7 +411,7 @@ def gpu_local_cpus(torch):
 
 
 # DRAM traffic of the FP64 product kernel, from a small case that ncu can capture
-# within its size rule: one solve of tridiag U[-1, 1], n = 8192 (a few GB on the
+# within its size rule: one solve of tridiag U[-1, 1], n = 8192, leaf 8 (a few GB on the
 # device), DRAM bytes read + written by the three k_gemm_fp64 launches of its top three
 # tree levels, divided by those levels' algorithmic bytes (Q_sel read + U written, the
 # per-level product_min_bytes that the same run records).  The capture and its command
@@ -420,10 +420,10 @@ def gpu_local_cpus(torch):
 # n = 32768, where the traffic per launch is the ratio times the algorithmic bytes per
 # launch.  A kernel whose source has changed since the capture reports no traffic.
 TRAFFIC_RATIO = {
-    # levels 5-7 at n = 8192: DRAM 729088 + 369152 + 295424 bytes read, 0 written, against
-    # 9043968 + 9388032 + 9175040 algorithmic bytes (the working set stays in L2)
-    "k_gemm_fp64": (1393664 / 27607040, "paper_1612_07526_gb300/csrc/gemm_fp64.cu",
-                    "cf209cc44828bcc6e213924409510e28463ef56048328b18eb355e2e62150381"),
+    # the top three levels (7-9) at n = 8192, leaf 8: DRAM 728832 + 379136 + 326400 bytes read,
+    # 0 written, against 9043968 + 9388032 + 9175040 algorithmic bytes (the working set stays in L2)
+    "k_gemm_fp64": (1434368 / 27607040, "paper_1612_07526_gb300/csrc/gemm_fp64.cu",
+                    "ad24dfc79a2604040226522cf558a7a6e55f241a93f8f64c3e053d07cf2fd840"),
 }
 
 

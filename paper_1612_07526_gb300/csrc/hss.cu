@@ -70,6 +70,12 @@ __device__ __forceinline__ double fetch(const HOp& op, const QhatSrc& q, const H
 
 constexpr int TB = 64, TK = 16;
 
+// Whether consecutive k of an operand are adjacent in memory (then the tile loader
+// walks k fastest across threads, else the row / column index), so that a warp's loads
+// fall on few cache lines.  A is read as a(r, k), B as b(k, c).
+__device__ __forceinline__ bool a_k_contiguous(int mode) { return mode == HOP_DENSE_T || mode == HOP_QHAT_T; }
+__device__ __forceinline__ bool b_k_contiguous(int mode) { return mode != HOP_DENSE_T && mode != HOP_QHAT_T; }
+
 __global__ __launch_bounds__(256) void k_hss_gemm(const HGemm* __restrict__ jobs, int njobs,
                                                   const int64_t* __restrict__ cum, QhatSrc q, HssCols xc) {
   __shared__ double As[TK][TB + 1];
@@ -90,13 +96,17 @@ __global__ __launch_bounds__(256) void k_hss_gemm(const HGemm* __restrict__ jobs
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  const bool ak = a_k_contiguous(G.a.mode), bk = b_k_contiguous(G.b.mode);   // uniform per job
   for (int k0 = 0; k0 < Kd; k0 += TK) {
     for (int e = tid; e < TK * TB; e += 256) {
-      const int kk = e / TB, rr = e % TB;
+      const int kk = ak ? e % TK : e / TB, rr = ak ? e / TK : e % TB;
       const int r = r0 + rr, k = k0 + kk;
       As[kk][rr] = (r < M && k < Kd) ? fetch(G.a, q, xc, r, k) : 0.0;
-      const int c = c0 + rr;
-      Bs[kk][rr] = (c < N && k < Kd) ? fetch(G.b, q, xc, k, c) : 0.0;
+    }
+    for (int e = tid; e < TK * TB; e += 256) {
+      const int kk = bk ? e % TK : e / TB, cc = bk ? e / TK : e % TB;
+      const int c = c0 + cc, k = k0 + kk;
+      Bs[kk][cc] = (c < N && k < Kd) ? fetch(G.b, q, xc, k, c) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -232,34 +242,41 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
       }
     }
     __syncthreads();
-    // Householder vector of M[k:, k]
-    if (tid == 0) {
+    // Householder vector of M[k:, k] (warp 0, lanes over the rows of the sample)
+    const int lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
+    if (wid == 0) {
+      double* colk = Mx + (int64_t)k * rp;
       double s = 0.0;
-      for (int r = k; r < rp; ++r) s += Mx[(int64_t)k * rp + r] * Mx[(int64_t)k * rp + r];
-      const double x0 = Mx[(int64_t)k * rp + k];
+      for (int r = k + lane; r < rp; r += 32) s = fma(colk[r], colk[r], s);
+      s = warp_sum(s);
+      const double x0 = colk[k];
       const double alpha = x0 >= 0.0 ? -sqrt(s) : sqrt(s);
       double vv = 0.0;
-      for (int r = k; r < rp; ++r) {
-        v[r] = Mx[(int64_t)k * rp + r] - (r == k ? alpha : 0.0);
-        vv += v[r] * v[r];
+      for (int r = k + lane; r < rp; r += 32) {
+        const double vr = colk[r] - (r == k ? alpha : 0.0);
+        v[r] = vr;
+        vv = fma(vr, vr, vv);
       }
-      s_red[1] = vv > 0.0 ? 2.0 / vv : 0.0;
-      Mx[(int64_t)k * rp + k] = alpha;
-      for (int r = k + 1; r < rp; ++r) Mx[(int64_t)k * rp + r] = 0.0;
+      vv = warp_sum(vv);
+      if (lane == 0) s_red[1] = vv > 0.0 ? 2.0 / vv : 0.0;
+      for (int r = k + lane; r < rp; r += 32) colk[r] = r == k ? alpha : 0.0;
     }
     __syncthreads();
     const double beta = s_red[1];
-    for (int c = k + 1 + tid; c < rows; c += NT) {
+    // the reflection of the remaining columns, a warp per column
+    for (int c = k + 1 + wid; c < rows; c += nw) {
       double* col = Mx + (int64_t)c * rp;
       double wdot = 0.0;
-      for (int r = k; r < rp; ++r) wdot += v[r] * col[r];
-      wdot *= beta;
+      for (int r = k + lane; r < rp; r += 32) wdot = fma(v[r], col[r], wdot);
+      wdot = warp_sum(wdot) * beta;
       double s = 0.0;
-      for (int r = k; r < rp; ++r) {
-        col[r] -= wdot * v[r];
-        if (r > k) s += col[r] * col[r];
+      for (int r = k + lane; r < rp; r += 32) {
+        const double x = col[r] - wdot * v[r];
+        col[r] = x;
+        if (r > k) s = fma(x, x, s);
       }
-      nrm[c] = s;
+      s = warp_sum(s);
+      if (lane == 0) nrm[c] = s;
     }
     __syncthreads();
   }
@@ -274,15 +291,21 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
   }
   __syncthreads();
   for (int t = tid; t < rank; t += NT) Jb.U[(int64_t)t * Jb.rows_max + perm[t]] = 1.0;
-  // T = R11^-1 R12, one column c of R12 per thread (back substitution)
-  for (int c = rank + tid; c < rows; c += NT) {
-    double* col = Mx + (int64_t)c * rp;     // R12 column, solved in place (rows 0..rank)
-    for (int r = rank - 1; r >= 0; --r) {
-      double s = col[r];
-      for (int q = r + 1; q < rank; ++q) s -= Mx[(int64_t)q * rp + r] * col[q];
-      col[r] = s / Mx[(int64_t)r * rp + r];
+  // T = R11^-1 R12, a warp per column c of R12 (back substitution, lanes over the
+  // solved entries of each step)
+  {
+    const int lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
+    for (int c = rank + wid; c < rows; c += nw) {
+      double* col = Mx + (int64_t)c * rp;   // R12 column, solved in place (rows 0..rank)
+      for (int r = rank - 1; r >= 0; --r) {
+        double s = 0.0;
+        for (int q = r + 1 + lane; q < rank; q += 32) s = fma(Mx[(int64_t)q * rp + r], col[q], s);
+        s = warp_sum(s);
+        if (lane == 0) col[r] = (col[r] - s) / Mx[(int64_t)r * rp + r];
+        __syncwarp();
+      }
+      for (int t = lane; t < rank; t += 32) Jb.U[(int64_t)t * Jb.rows_max + perm[c]] = col[t];
     }
-    for (int t = 0; t < rank; ++t) Jb.U[(int64_t)t * Jb.rows_max + perm[c]] = col[t];
   }
 }
 
