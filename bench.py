@@ -320,7 +320,27 @@ def context_measurements(api, _lib, lib, torch):
                                        "achieved_tflops": p.secular_flops / (p.ms[2] * 1e-3) / 1e12}
     ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
                            "status_nonzero": int((plan.status != 0).sum()),
-                           "tile_shapes": ",".join(map(str, shapes))}
+                           "tile_shapes": ",".join(map(str, shapes)),
+                           "launch": "one launch per phase per tree level, captured in a CUDA graph"}
+    # the same batch as ONE persistent kernel launch (each CTA takes whole problems from a
+    # work queue, largest first), captured in a graph and replayed
+    lam_p, q_p = plan.outputs()
+    plan.capture(d_cat, e_cat, lam_p, q_p, persistent=True)
+    for _ in range(2):
+        plan.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.replay()
+    e1.record()
+    e1.synchronize()
+    ms_p = e0.elapsed_time(e1) / reps
+    ctx["batched_4096_persistent"] = {"ms": ms_p, "problems_per_s": 4096 / (ms_p * 1e-3),
+                                      "status_nonzero": int((plan.status != 0).sum()),
+                                      "max_abs_lambda_diff_vs_level_launches": float((lam_p - lam).abs().max()),
+                                      "launch": "one persistent kernel (after 4 memsets), captured in a CUDA graph"}
+    del lam_p, q_p
     del plan, q, lam
     torch.cuda.empty_cache()
     ctx["backward_batched_64x4096"] = backward_measurement(api, _lib, lib, torch)

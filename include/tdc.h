@@ -352,6 +352,21 @@ int tdc_batched_plan_execute(const tdc_batched_plan* plan, const double* d_cat, 
 void tdc_batched_plan_destroy(tdc_batched_plan* plan);
 
 /*
+ * tdc_batched_plan_execute_persistent -- the same solve as tdc_batched_plan_execute in ONE
+ * kernel launch (after four status / counter memsets): every CTA of a grid of
+ * (SMs x resident CTAs) takes whole problems from a work queue, largest first, and runs
+ * all their phases -- tear (Eq. 2), leaves, and each merge bottom-up (Eqs. 3-6) -- with
+ * block barriers only; no CTA waits on another.  Same layout, outputs and status words as
+ * tdc_batched_plan_execute; capturable in a CUDA graph.  The FP64 product only (64 x 16
+ * tiles; the lanes per secular root follow each merge's K, so results agree with the
+ * level-by-level execute to rounding, not bit for bit).  Returns 0, -i for a bad argument
+ * i (-1 also for a plan on another product path), or 4 for a launch error.
+ */
+int tdc_batched_plan_execute_persistent(const tdc_batched_plan* plan, const double* d_cat, const double* e_cat,
+                                        double* lambda_cat, double* Q_cat, int* dev_status_per_problem,
+                                        void* stream);
+
+/*
  * tdc_batched_plan_execute_host -- one execute of the plan between host buffers,
  * without waiting: enqueues on `stream` the copies of d_host, e_host (the plan's dense
  * packing, sum(n) doubles each, e padded by one zero per problem) into the caller's

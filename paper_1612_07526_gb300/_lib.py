@@ -98,6 +98,7 @@ SIGNATURES = [
                                                ctypes.POINTER(ctypes.c_void_p)]),
     ("tdc_batched_plan_execute", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("tdc_batched_plan_destroy", None, [_P]),
+    ("tdc_batched_plan_execute_persistent", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("tdc_batched_plan_execute_host", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("tdc_syev_tridiag_backward", ctypes.c_int, [_I64, _P, _P, _I64, _P, _P, _I64, _P, _P, _OPT, _P,
                                                  ctypes.c_size_t, _P, _P]),

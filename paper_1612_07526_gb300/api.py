@@ -471,8 +471,24 @@ class BatchedPlan:
         _check_rc(rc, "tdc_batched_plan_autotune")
         return [int(shapes[i]) for i in range(min(nl.value, 64))]
 
-    def capture(self, d_cat, e_cat, lam, q):
-        """Captures one execute on these buffers into a CUDA graph (after a warm-up)."""
+    def execute_persistent(self, d_cat, e_cat, lam, q, stream=None):
+        """The same solve in one persistent kernel launch (tdc_batched_plan_execute_persistent:
+        each CTA takes whole problems from a work queue; FP64 product plans only)."""
+        rc = self.lib.tdc_batched_plan_execute_persistent(self.handle, _vp(d_cat), _vp(e_cat), _vp(lam), _vp(q),
+                                                          _vp(self.status), _stream(stream))
+        _check_rc(rc, "tdc_batched_plan_execute_persistent")
+
+    def capture(self, d_cat, e_cat, lam, q, persistent=False):
+        """Captures one execute (or one persistent execute) on these buffers into a CUDA
+        graph (after a warm-up)."""
+        if persistent:
+            self.execute_persistent(d_cat, e_cat, lam, q)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.execute_persistent(d_cat, e_cat, lam, q)
+            self.graph = g
+            return
         self.execute(d_cat, e_cat, lam, q)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()

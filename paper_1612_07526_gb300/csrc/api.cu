@@ -35,11 +35,52 @@ struct Plan {
   std::vector<int64_t> tear_list, tear_ptr;
   std::vector<LevelPlan> levels;
   std::vector<int64_t> sign_qoff, sign_n, sign_ld, sign_cum;
+  // the persistent kernel's view: problems largest first, each problem's merges bottom-up
+  std::vector<PersistProb> pprobs;
+  std::vector<MergeJob> pmerges;
+  std::vector<int32_t> pmlev;
   int64_t nmerges = 0;
   int64_t maxm = 0;
   size_t o_leaves = 0, o_tlist = 0, o_tptr = 0, o_sq = 0, o_sn = 0, o_sl = 0, o_sc = 0;
+  size_t o_pprobs = 0, o_pmerges = 0, o_pmlev = 0;
   std::vector<unsigned char> blob;
 };
+
+// Per problem: its leaves (contiguous in the leaf list: the tree is built problem by
+// problem), tear points and merges in level order; problems sorted by order,
+// largest first, so the persistent kernel's work queue ends on small problems.
+static void persistent_lists(Plan& P, int nprob, const std::vector<int64_t>& vbase, const std::vector<int64_t>& nvec) {
+  std::vector<std::vector<std::pair<MergeJob, int32_t>>> per(nprob);
+  for (size_t l = 0; l < P.levels.size(); ++l)
+    for (const MergeJob& J : P.levels[l].jobs) per[J.prob].push_back({J, (int32_t)l});
+  std::vector<int64_t> leaf0(nprob, -1), nleaf(nprob, 0);
+  for (size_t i = 0; i < P.leaves.size(); ++i) {
+    const int p = P.leaves[i].prob;
+    if (leaf0[p] < 0) leaf0[p] = (int64_t)i;
+    ++nleaf[p];
+  }
+  P.pprobs.clear();
+  P.pmerges.clear();
+  P.pmlev.clear();
+  for (int p = 0; p < nprob; ++p) {
+    PersistProb q{};
+    q.v0 = vbase[p];
+    q.n = nvec[p];
+    q.leaf0 = leaf0[p] < 0 ? 0 : leaf0[p];
+    q.nleaf = (int32_t)nleaf[p];
+    q.tear0 = P.tear_ptr[p];
+    q.tear1 = P.tear_ptr[p + 1];
+    q.merge0 = (int64_t)P.pmerges.size();
+    q.nmerge = (int32_t)per[p].size();
+    for (const auto& jm : per[p]) {
+      P.pmerges.push_back(jm.first);
+      P.pmlev.push_back(jm.second);
+    }
+    P.pprobs.push_back(q);
+  }
+  std::stable_sort(P.pprobs.begin(), P.pprobs.end(),
+                   [](const PersistProb& a, const PersistProb& b) { return a.n > b.n; });
+}
 
 static int build_node(Plan& P, const ProblemDesc& pd, int prob, int64_t lo, int64_t n, int depth,
                       int leaf) {
@@ -117,6 +158,9 @@ static void finish_plan(Plan& P) {
   P.o_sn = blob_put(P.blob, P.sign_n);
   P.o_sl = blob_put(P.blob, P.sign_ld);
   P.o_sc = blob_put(P.blob, P.sign_cum);
+  P.o_pprobs = blob_put(P.blob, P.pprobs);
+  P.o_pmerges = blob_put(P.blob, P.pmerges);
+  P.o_pmlev = blob_put(P.blob, P.pmlev);
   for (auto& L : P.levels) {
     L.o_jobs = blob_put(P.blob, L.jobs);
     L.o_cw8 = blob_put(P.blob, L.cw8);
@@ -130,6 +174,7 @@ static void finish_plan(Plan& P) {
 static void build_plan(Plan& P, const std::vector<ProblemDesc>& probs, int leaf) {
   P.tear_ptr.push_back(0);
   P.sign_cum.push_back(0);
+  std::vector<int64_t> vbase(probs.size()), nvec(probs.size());
   for (size_t p = 0; p < probs.size(); ++p) {
     const ProblemDesc& pd = probs[p];
     if (pd.n > 0) build_node(P, pd, (int)p, 0, pd.n, 0, leaf);
@@ -138,7 +183,10 @@ static void build_plan(Plan& P, const std::vector<ProblemDesc>& probs, int leaf)
     P.sign_n.push_back(pd.n);
     P.sign_ld.push_back(pd.lda);
     P.sign_cum.push_back(P.sign_cum.back() + pd.n);
+    vbase[p] = pd.vbase;
+    nvec[p] = pd.n;
   }
+  persistent_lists(P, (int)probs.size(), vbase, nvec);
   finish_plan(P);
 }
 
@@ -159,6 +207,7 @@ struct Carver {
 
 struct Layout {
   DevWs w{};
+  unsigned* queue = nullptr;  // the persistent kernel's work counter
   double* pool = nullptr;     // the problems' pools: 3 n x n per problem
   unsigned char* plan = nullptr;
   unsigned char* arena = nullptr;
@@ -225,6 +274,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.lroti = c.take<uint8_t>(NL * kLeafRot);
   w.lrotn = c.take<int32_t>(NL);
   w.status = c.take<int>((size_t)std::max(nprob, 1));
+  L.queue = c.take<unsigned>(64);
   L.plan = c.take<unsigned char>(plan_bytes);
   L.table = c.take<unsigned char>(ps.table_bytes);
   L.arena = c.take<unsigned char>(ps.arena_bytes);
@@ -1069,6 +1119,31 @@ int tdc_batched_plan_autotune(tdc_batched_plan* h, const double* d_cat, const do
   const int rc = autotune_plan(h->P, h->pp, h->L, h->o, d_cat, e_cat, lambda_cat, qb, h->vtot, h->batch, st, best);
   if (rc) return rc;
   copy_shapes(best, shape_per_level, max_levels, n_levels);
+  return launch_status();
+}
+
+int tdc_batched_plan_execute_persistent(const tdc_batched_plan* h, const double* d_cat, const double* e_cat,
+                                        double* lambda_cat, double* Q_cat, int* dev_status_per_problem,
+                                        void* stream) {
+  if (!h) return -1;
+  if (!d_cat) return -2;
+  if (!e_cat) return -3;
+  if (!lambda_cat) return -4;
+  if (!Q_cat) return -5;
+  if (h->o.path != TDC_PATH_DENSE_FP64) return -1;   // the FP64 product only
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L = h->L;
+  if (dev_status_per_problem) L.w.status = dev_status_per_problem;
+  L.w.ext = h->o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
+  const Plan& P = h->P;
+  cudaMemsetAsync(L.w.status, 0, sizeof(int) * h->batch, st);
+  cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.scal, 0, std::max<int64_t>(P.nmerges, 1) * sizeof(MergeScalars), st);
+  cudaMemsetAsync(L.queue, 0, sizeof(unsigned), st);
+  QBufs qb{Q_cat, L.pool, nullptr};
+  launch_batched_persistent(P_<PersistProb>(L, P.o_pprobs), (int)P.pprobs.size(), L.queue,
+                            P_<LeafJob>(L, P.o_leaves), P_<int64_t>(L, P.o_tlist), P_<MergeJob>(L, P.o_pmerges),
+                            P_<int32_t>(L, P.o_pmlev), d_cat, e_cat, lambda_cat, qb, L.w, h->o.max_secular_iter, st);
   return launch_status();
 }
 

@@ -56,6 +56,16 @@ struct MergeJob {
   int32_t ext;       // 1: the inputs are the caller's block-diagonal Q (tdc_merge), not the slot table
 };
 
+// A problem of a batch as the persistent kernel sees it (the plan lists these largest
+// first): its vectors, leaves, tear points and merges (in bottom-up level order).
+struct PersistProb {
+  int64_t v0, n;         // first index and order
+  int64_t leaf0;         // first of its leaves in the plan's leaf list
+  int64_t tear0, tear1;  // its tear points in the plan's tear list
+  int64_t merge0;        // first of its merges in the persistent merge list
+  int32_t nleaf, nmerge;
+};
+
 struct MergeScalars {
   int32_t K;         // non-deflated count
   int32_t c1, c3;    // Gu groups: columns touching rows of T1 only / both halves
@@ -234,5 +244,13 @@ void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_w8, in
 
 
 constexpr int kGemmShapes = 12;
+
+// The persistent batched solve: one launch; every CTA takes whole problems from a work
+// queue (largest first) and runs all of their phases itself, so no CTA waits on another.
+// queue: a device counter the caller zeroes before the launch; w.scal zeroed likewise.
+void launch_batched_persistent(const PersistProb* probs, int nprob, unsigned* queue, const LeafJob* leaves,
+                               const int64_t* tear_list, const MergeJob* pmerges, const int32_t* pmlev,
+                               const double* d, const double* e, double* lam, QBufs qb, DevWs w, int max_iter,
+                               cudaStream_t st);
 
 }  // namespace tdc
