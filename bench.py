@@ -272,6 +272,10 @@ def context_measurements(api, _lib, lib, torch):
     ctx["toeplitz_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64", exact=ex)
     ctx["toeplitz_16384_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", exact=ex)
     ctx["toeplitz_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss", exact=ex)
+    # HSS with 256-leaves and 64 starting samples (grown where a rank reaches them): fewer
+    # FP64 flops in the sampling and the leaf blocks of the multiply, a looser residual
+    ctx["toeplitz_16384_hss_leaf256_rp64"] = profiled_solve(api, _lib, lib, torch, d, e, "hss", exact=ex,
+                                                            hss_leaf=256, hss_rp=64)
     d, e = W.normal_tridiag(16384, 0)
     ctx["normal_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64")
     ctx["normal_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss")
@@ -438,12 +442,14 @@ def gpu_local_cpus(torch):
 # are summarised under profiles/.  The product reads each selected column of Q once
 # and writes each output column once whatever n is, so the ratio carries over to
 # n = 32768, where the traffic per launch is the ratio times the algorithmic bytes per
-# launch.  A kernel whose source has changed since the capture reports no traffic.
+# launch.  A kernel whose source files (all of them) have changed since the capture
+# reports no traffic.
 TRAFFIC_RATIO = {
     # the top three levels (7-9) at n = 8192, leaf 8: DRAM 728832 + 379136 + 326400 bytes read,
     # 0 written, against 9043968 + 9388032 + 9175040 algorithmic bytes (the working set stays in L2)
-    "k_gemm_fp64": (1434368 / 27607040, "paper_1612_07526_gb300/csrc/gemm_fp64.cu",
-                    "ad24dfc79a2604040226522cf558a7a6e55f241a93f8f64c3e053d07cf2fd840"),
+    "k_gemm_fp64": (1434368 / 27607040,
+                    (("paper_1612_07526_gb300/csrc/gemm_fp64.cu", "77ca22faebba88f56e0fdf2de8ee79efeddd6d3d6dce1dd896dc2f7353fe1bd2"),
+                     ("paper_1612_07526_gb300/csrc/tdc_gemm_tile.cuh", "836078dcdb591b869d10646d2f2d04fd2b39f4e23d3551a8b68be960f55b228d"))),
 }
 
 
@@ -454,13 +460,14 @@ def measured_traffic(kernel, alg_bytes_per_launch):
     rec = TRAFFIC_RATIO.get(kernel)
     if rec is None or not alg_bytes_per_launch:
         return None
-    ratio, src, sha = rec
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), src), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != sha:
-                return None
-    except OSError:
-        return None
+    ratio, sources = rec
+    for src, sha in sources:                   # every file holding the kernel's code, unchanged
+        try:
+            with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
     return ratio * alg_bytes_per_launch
 
 

@@ -19,12 +19,17 @@ def test_traffic_needs_a_record_of_the_current_source(monkeypatch):
     src = "paper_1612_07526_gb300/csrc/gemm_fp64.cu"
     with open(os.path.join(root, src), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    monkeypatch.setattr(bench, "TRAFFIC_RATIO", {"k_gemm_fp64": (1.25, src, sha)})
+    monkeypatch.setattr(bench, "TRAFFIC_RATIO", {"k_gemm_fp64": (1.25, ((src, sha),))})
     assert bench.measured_traffic("k_gemm_fp64", 1000.0) == 1250.0
     assert bench.measured_traffic("k_oz_gemm", 1000.0) is None
     assert bench.measured_traffic("k_gemm_fp64", 0.0) is None
-    monkeypatch.setattr(bench, "TRAFFIC_RATIO", {"k_gemm_fp64": (1.25, src, "0" * 64)})
-    assert bench.measured_traffic("k_gemm_fp64", 1000.0) is None       # the kernel changed since
+    monkeypatch.setattr(bench, "TRAFFIC_RATIO", {"k_gemm_fp64": (1.25, ((src, sha), (src, "0" * 64)))})
+    assert bench.measured_traffic("k_gemm_fp64", 1000.0) is None       # a kernel file changed since
+
+
+def test_traffic_record_matches_the_current_kernel_sources():
+    """The committed record was captured on the product kernel as it is now."""
+    assert bench.measured_traffic("k_gemm_fp64", 1000.0) is not None
 
 
 def test_both_arms_print_the_same_config():
