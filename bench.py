@@ -321,7 +321,8 @@ def context_measurements(api, _lib, lib, torch):
     ctx["batched_4096_phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES) if p.ms[i] > 0}
     if p.secular_flops > 0 and p.ms[2] > 0:
         ctx["batched_4096_secular"] = {"algorithmic_tflop": p.secular_flops / 1e12,
-                                       "achieved_tflops": p.secular_flops / (p.ms[2] * 1e-3) / 1e12}
+                                       "achieved_tflops": p.secular_flops / (p.ms[2] * 1e-3) / 1e12,
+                                       "fp64_evals_per_root": p.secular_evals / max(p.K_total, 1)}
     ctx["batched_4096"] = {"ms": ms, "problems_per_s": 4096 / (ms * 1e-3), "sum_n": int(sizes.sum()),
                            "status_nonzero": int((plan.status != 0).sum()),
                            "tile_shapes": ",".join(map(str, shapes)),
@@ -746,8 +747,9 @@ def main():
         cands.append({"bound": "alu", "achieved": prof.secular_flops / (prof.ms[2] * 1e-3) / 1e12,
                       "peak": fp64_peak, "unit": "TFLOP/s", "ms_per_step": prof.ms[2] / args.steps,
                       "kernel": "k_secular / k_secular_grp: secular roots, a warp per root, or 4-16 lanes "
-                                "per root on levels with enough roots (K terms per evaluation: "
-                                "1 division + 3 FMA)",
+                                "per root on levels with enough roots (K terms per FP64 evaluation: "
+                                "1 division + 4 FMA + 1 multiplication)",
+                      "fp64_evals_per_root": prof.secular_evals / max(prof.K_total, 1),
                       "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
                       "algorithmic_per_step": prof.secular_flops / args.steps})
     # per tree level (leaves up), per step: the FP64 product's algorithmic bytes and flops
@@ -794,7 +796,8 @@ def main():
         "roofline_other": cands[1:],
         "cpu_baseline": cpu,
         "phases": phases,
-        "merge_stats": {"merges_per_step": prof.merges / args.steps, "K_total_per_step": prof.K_total / args.steps},
+        "merge_stats": {"merges_per_step": prof.merges / args.steps, "K_total_per_step": prof.K_total / args.steps,
+                        "secular_fp64_evals_per_root": prof.secular_evals / max(prof.K_total, 1)},
         "product_eff_tflops": achieved,
         "accuracy": acc,
         "clocks": clk_sum,

@@ -61,7 +61,7 @@ typedef struct tdc_opts {
                              /* rule), 0..11 = 128x128, 128x64, 64x64, 64x32, 32x32,   */
                              /* 128x32, 64x16, 128x16, 16x16, 16x32, 16x64, 32x16       */
   int32_t secular_lanes;     /* lanes per secular root: 0 = chosen per tree level from  */
-                             /* the level's root count (default), or 4, 8, 16, 32        */
+                             /* the level's root count (default), or 1, 2, 4, 8, 16, 32 */
   int32_t eigvec;            /* how the eigenvectors of D + rho z z^T keep orthogonal    */
                              /* (Section 1): TDC_EIGVEC_LOWNER (default) or             */
                              /* TDC_EIGVEC_EXTENDED                                       */
@@ -294,8 +294,9 @@ typedef struct tdc_profile {
   double split_tensor_flops;       /* bf16 tensor flops those run: slice pairs x 2 m K K */
   double defl_copy_bytes;          /* top merges: 8 bytes x rows x deflated columns
                                       written plus 8 bytes x their live rows read         */
-  double secular_flops;            /* 7 K x (secular-function evaluations) per merge:
-                                      K terms of one division and three FMA each        */
+  double secular_flops;            /* 10 K x (FP64 secular-function evaluations) per
+                                      merge: K terms of one division, four FMA and one
+                                      multiplication each                                */
   int64_t hss_fallbacks;           /* HSS merges whose ID ranks reached the sample count
                                       (r + p) even after the adaptive growths and that
                                       took the dense product instead                      */
@@ -306,6 +307,8 @@ typedef struct tdc_profile {
   double level_fp64_flops[TDC_PROFILE_LEVELS];       /* the same for fp64_product_flops  */
   double level_fp64_product_ms[TDC_PROFILE_LEVELS];  /* event time of each level's FP64
                                                         product (tile count + GEMM)        */
+  int64_t secular_evals;           /* FP64 secular-function evaluations, summed over the
+                                      roots (the FP32 evaluations are not counted)        */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);

@@ -56,6 +56,7 @@ class TdcProfile(ctypes.Structure):
         ("level_fp64_min_bytes", ctypes.c_double * 32),
         ("level_fp64_flops", ctypes.c_double * 32),
         ("level_fp64_product_ms", ctypes.c_double * 32),
+        ("secular_evals", ctypes.c_int64),
     ]
 
 

@@ -226,7 +226,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.zs = c.take<double>(N);
   w.dbar = c.take<double>(N);
   w.zbar = c.take<double>(N);
-  w.dbar32 = c.take<float>(N);
+  w.dbar32 = c.take<float2>(N);
   w.zbar32 = c.take<float>(N);
   w.zhat = c.take<double>(N);
   w.tau = c.take<double>(N);
@@ -293,8 +293,8 @@ static bool opts_valid(const tdc_opts& o) {
   return o.path >= TDC_PATH_DENSE_FP64 && o.path <= TDC_PATH_AUTO && o.leaf >= 1 && o.leaf <= 32 &&
          o.max_secular_iter >= 1 && o.ozaki_slices >= 5 && o.ozaki_slices <= 7 && o.hss_leaf >= 16 &&
          o.hss_rp >= 8 && o.hss_tol > 0.0 &&
-         (o.secular_lanes == 0 || o.secular_lanes == 4 || o.secular_lanes == 8 || o.secular_lanes == 16 ||
-          o.secular_lanes == 32) &&
+         (o.secular_lanes == 0 || o.secular_lanes == 1 || o.secular_lanes == 2 || o.secular_lanes == 4 ||
+          o.secular_lanes == 8 || o.secular_lanes == 16 || o.secular_lanes == 32) &&
          (o.eigvec == TDC_EIGVEC_LOWNER || o.eigvec == TDC_EIGVEC_EXTENDED) && o.hss_grow >= 0 &&
          o.hss_grow <= 4;
 }
@@ -440,6 +440,7 @@ struct ProfState {
   int64_t launches[TDC_NPHASE] = {};
   double flops = 0.0, bytes = 0.0, fp64_flops = 0.0, split_flops = 0.0, tensor_flops = 0.0, copy_bytes = 0.0;
   double secular_flops = 0.0;
+  int64_t secular_evals = 0;
   int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0, hss_regrowths = 0;
   double hss_sampling_flops = 0.0;
   double lvl_bytes[TDC_PROFILE_LEVELS] = {}, lvl_flops[TDC_PROFILE_LEVELS] = {};
@@ -526,7 +527,8 @@ static void prof_account(const Plan& P, const PathPlan& pp, const MergeScalars* 
       }
       g_prof.bytes += 8.0 * (J.n1 * (c1 + c3) + J.n2 * (c3 + c2) + m * K);
       if (J.fin) g_prof.copy_bytes += 8.0 * m * (m - K) + 8.0 * (double)S.live;   // columns written, live rows read
-      g_prof.secular_flops += 7.0 * K * (double)S.evals;      // K terms per evaluation: 1 division, 3 FMA
+      g_prof.secular_flops += 10.0 * K * (double)S.evals;     // K terms per evaluation: 1 division, 4 FMA, 1 mul
+      g_prof.secular_evals += (int64_t)S.evals;
       g_prof.merges += 1;
       g_prof.ktot += S.K;
     }
@@ -963,6 +965,7 @@ void tdc_profile_begin(void) {
   for (int i = 0; i < TDC_NPHASE; ++i) g_prof.launches[i] = 0;
   g_prof.flops = g_prof.bytes = g_prof.fp64_flops = g_prof.split_flops = g_prof.tensor_flops = 0.0;
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
+  g_prof.secular_evals = 0;
   g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = g_prof.hss_regrowths = 0;
   g_prof.hss_sampling_flops = 0.0;
   for (int i = 0; i < TDC_NPHASE + TDC_PROFILE_LEVELS; ++i) g_prof.open_ev[i] = nullptr;
@@ -990,6 +993,7 @@ int tdc_profile_end(tdc_profile* out) {
   out->split_tensor_flops = g_prof.tensor_flops;
   out->defl_copy_bytes = g_prof.copy_bytes;
   out->secular_flops = g_prof.secular_flops;
+  out->secular_evals = g_prof.secular_evals;
   out->hss_fallbacks = g_prof.hss_fallbacks;
   out->hss_regrowths = g_prof.hss_regrowths;
   out->hss_sampling_flops = g_prof.hss_sampling_flops;

@@ -86,7 +86,8 @@ struct MergeScalars {
 struct DevWs {
   double *ds, *zs;            // sorted d and z (updated by rotations)
   double *dbar, *zbar;        // non-deflated (K) values
-  float *dbar32, *zbar32;     // their FP32 copies (the secular solver's FP32 phase)
+  float2 *dbar32;             // d as FP32 pairs (hi, lo), d = hi + lo (the secular solver's FP32 phase)
+  float *zbar32;              // z in FP32
   double *zhat, *tau, *sinv, *cmax;
   double *taulo;              // extended-precision eigenvectors: the roots' low parts (tau + taulo)
   double *lamnd;              // non-deflated eigenvalues d_org + tau

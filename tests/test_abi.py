@@ -58,7 +58,7 @@ def test_host_side_argument_checks(lib):
     bad = _lib.default_opts(leaf=0)
     assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(bad), P(256), 1 << 20, None, None) == -7
     assert o.secular_lanes == 0
-    for lanes in (1, 2, 3, 64, -1):
+    for lanes in (3, 5, 64, -1):
         bad = _lib.default_opts(secular_lanes=lanes)
         assert lib.tdc_syev_tridiag(4, P(8), P(8), P(8), P(8), 4, ctypes.byref(bad), P(256), 1 << 20,
                                     None, None) == -7

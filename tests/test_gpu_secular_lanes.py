@@ -1,4 +1,4 @@
-"""Secular roots with 4, 8, 16 or 32 lanes per root (Section 1's secular equation).
+"""Secular roots with 1, 2, 4, 8, 16 or 32 lanes per root (Section 1's secular equation).
 
 Each mapping is forced through tdc_opts.secular_lanes and checked against the
 oracle (the DC oracle's eigenpairs, Sturm-count bisection for the eigenvalues) on
@@ -35,7 +35,7 @@ def _gen(gen, n):
     return W.normal_tridiag(n, 22)
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("gen,n", [("uniform", 700), ("normal", 1000), ("toeplitz", 600), ("normal", 45)])
 def test_forced_lanes_match_oracle(api, lanes, gen, n):
     d, e = _gen(gen, n)
@@ -57,7 +57,7 @@ def test_bad_lanes_rejected(api):
     d, e = W.normal_tridiag(50, 1)
     with pytest.raises(ValueError):
         api.syev_tridiag(torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda"),
-                         opts={"secular_lanes": 2})
+                         opts={"secular_lanes": 3})
 
 
 def test_auto_lanes_large_batch(api):
