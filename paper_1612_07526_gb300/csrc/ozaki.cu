@@ -289,53 +289,109 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
 }
 
 // ------------------------------------------------------------------------ generated, sliced Qhat
+// Blocks strided over the level's schedule (cum from k_oz_sched): column i < K of
+// Qhat, k range [2048 kc, 2048 kc + 2048) of its padded length KP.
 template <int S>
 __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__ jobs,
                                                     const OzJob* __restrict__ ozj, int njobs,
                                                     const int64_t* __restrict__ cum, DevWs w) {
-  const JobView jv = job_of(cum, njobs);
-  const MergeJob J = jobs[jv.jb];
-  const OzJob& Z = ozj[jv.jb];
-  const int m = J.n1 + J.n2;
-  const int64_t nkc = (Z.ldk + 2047) / 2048;
-  const int i = (int)(jv.local / nkc);
-  const int kc = (int)(jv.local % nkc);
-  const MergeScalars Sc = w.scal[J.mid];
-  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
-  if (i >= K || i >= m) return;
-  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
-  const int KP = P1 + P3 + P2;
-  const int64_t o = J.v_off;
-  const int32_t* __restrict__ kperm = w.kperm + o;
-  const double* __restrict__ wcol = w.wptr[o + i];     // unscaled column i of the Cauchy factor
-  const double si = w.sinv[o + i];
-  int e = 0;
-  const double cm = w.cmax[o + i];
-  if (cm > 0.0) frexp(cm, &e);
-  if (kc == 0 && threadIdx.x == 0) Z.texp[i] = e;
-  const int shift = 8 * S - 1 - e;
-  const int k0 = kc * 2048 + threadIdx.x * 8;
-  if (k0 >= Z.ldk) return;
-  uint16_t dg[8][S];
+  const int64_t total = cum[njobs];
+  for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int jb = find_job(cum, njobs, vb);
+    const int64_t local = vb - cum[jb];
+    const MergeJob J = jobs[jb];
+    const OzJob& Z = ozj[jb];
+    const int m = J.n1 + J.n2;
+    const MergeScalars Sc = w.scal[J.mid];
+    const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
+    const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
+    const int KP = P1 + P3 + P2;
+    const int64_t nkc = (KP + 2047) / 2048;
+    const int i = (int)(local / nkc);
+    const int kc = (int)(local % nkc);
+    const int64_t o = J.v_off;
+    const int32_t* __restrict__ kperm = w.kperm + o;
+    const double* __restrict__ wcol = w.wptr[o + i];     // unscaled column i of the Cauchy factor
+    const double si = w.sinv[o + i];
+    int e = 0;
+    const double cm = w.cmax[o + i];
+    if (cm > 0.0) frexp(cm, &e);
+    if (kc == 0 && threadIdx.x == 0) Z.texp[i] = e;
+    const int shift = 8 * S - 1 - e;
+    const int k0 = kc * 2048 + threadIdx.x * 8;
+    if (k0 >= KP) continue;
+    uint16_t dg[8][S];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int k = k0 + j;
-    const int kg = k < KP ? padded_to_grouped(k, c1, c3, K, P1, P3) : -1;
-    double v = 0.0;
-    if (kg >= 0) v = wcol[kperm[kg]] * si;
-    uint16_t tt[S];
-    digits_bf16<S>(round_scaled(v, shift), tt);
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j;
+      const int kg = padded_to_grouped(k, c1, c3, K, P1, P3);
+      double v = 0.0;
+      if (kg >= 0) v = wcol[kperm[kg]] * si;
+      uint16_t tt[S];
+      digits_bf16<S>(round_scaled(v, shift), tt);
 #pragma unroll
-    for (int p = 0; p < S; ++p) dg[j][p] = tt[p];
+      for (int p = 0; p < S; ++p) dg[j][p] = tt[p];
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      uint4 vv;
+      vv.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+      vv.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+      vv.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+      vv.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+      *reinterpret_cast<uint4*>(Z.b + ((int64_t)p * m + i) * Z.ldk + k0) = vv;
+    }
   }
-#pragma unroll
-  for (int p = 0; p < S; ++p) {
-    uint4 vv;
-    vv.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
-    vv.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
-    vv.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
-    vv.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
-    *reinterpret_cast<uint4*>(Z.b + ((int64_t)p * m + i) * Z.ldk + k0) = vv;
+}
+
+// The level's schedules from the merges' K (known only on the device): blocks of
+// k_oz_slice_b (K columns x cdiv(KP, 2048)) and tiles of k_oz_gemm ((row tiles of T1
+// + of T2) x cdiv(K, kOzBN)); cum[j] = units of the merges before j.  One block of
+// 1024 threads, each summing a contiguous run of merges, then a scan.
+__global__ __launch_bounds__(1024) void k_oz_sched(const MergeJob* __restrict__ jobs, int njobs,
+                                                   const MergeScalars* __restrict__ scal,
+                                                   int64_t* __restrict__ cum_sb, int64_t* __restrict__ cum_t) {
+  __shared__ int64_t part[2][1024];
+  const int t = threadIdx.x;
+  const int per = (njobs + 1023) / 1024;
+  const int j0 = min(t * per, njobs), j1 = min(j0 + per, njobs);
+  auto units = [&](int j, int64_t& sb, int64_t& tl) {
+    const MergeJob& J = jobs[j];
+    const MergeScalars& Sc = scal[J.mid];
+    const int K = Sc.K;
+    const int64_t KP = rup(Sc.c1, kOzPad) + rup(Sc.c3, kOzPad) + rup(K - Sc.c1 - Sc.c3, kOzPad);
+    sb = (int64_t)K * ((KP + 2047) / 2048);
+    tl = (int64_t)((J.n1 + kOzBM - 1) / kOzBM + (J.n2 + kOzBM - 1) / kOzBM) * ((K + kOzBN - 1) / kOzBN);
+  };
+  int64_t a = 0, b = 0;
+  for (int j = j0; j < j1; ++j) {
+    int64_t sb, tl;
+    units(j, sb, tl);
+    a += sb;
+    b += tl;
+  }
+  part[0][t] = a;
+  part[1][t] = b;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {      // inclusive Hillis-Steele scans
+    const int64_t va = t >= off ? part[0][t - off] : 0, vb = t >= off ? part[1][t - off] : 0;
+    __syncthreads();
+    part[0][t] += va;
+    part[1][t] += vb;
+    __syncthreads();
+  }
+  int64_t ra = t > 0 ? part[0][t - 1] : 0, rb = t > 0 ? part[1][t - 1] : 0;
+  for (int j = j0; j < j1; ++j) {
+    cum_sb[j] = ra;
+    cum_t[j] = rb;
+    int64_t sb, tl;
+    units(j, sb, tl);
+    ra += sb;
+    rb += tl;
+  }
+  if (t == 1023) {
+    cum_sb[njobs] = part[0][1023];
+    cum_t[njobs] = part[1][1023];
   }
 }
 
@@ -359,6 +415,41 @@ struct OzCfg {
   __host__ __device__ static constexpr int qmax(int p) { return S < S + 2 - p ? S : S + 2 - p; }
 };
 
+// One tile of the product: its merge, half (T1 or T2 rows), rows and columns, and the
+// k range of the Gu groups that half uses.
+struct OzTile {
+  int jb, h, row0, rows_h, rowbase, ct, kb, nst, nchunks, K;
+};
+__device__ __forceinline__ OzTile oz_tile(const MergeJob* __restrict__ jobs, const int64_t* __restrict__ cum,
+                                          int njobs, const DevWs& w, int64_t t) {
+  OzTile v;
+  v.jb = find_job(cum, njobs, t);
+  const int64_t local = t - cum[v.jb];
+  const MergeJob J = jobs[v.jb];
+  const MergeScalars Sc = w.scal[J.mid];
+  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
+  const int nct = (K + kOzBN - 1) / kOzBN;                 // >= 1: a merge with tiles has K > 0
+  const int nrt1 = (J.n1 + kOzBM - 1) / kOzBM;
+  v.K = K;
+  v.ct = (int)(local % nct);
+  const int rtl = (int)(local / nct);
+  v.h = rtl < nrt1 ? 0 : 1;
+  v.row0 = (v.h ? rtl - nrt1 : rtl) * kOzBM;               // within the half
+  v.rows_h = v.h ? J.n2 : J.n1;
+  v.rowbase = v.h ? J.n1 : 0;
+  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
+  const int klen = v.h ? P3 + P2 : P1 + P3;
+  v.kb = v.h ? P1 : 0;
+  v.nst = klen / kOzBK;
+  v.nchunks = (v.nst + kOzChunk / kOzBK - 1) / (kOzChunk / kOzBK);
+  return v;
+}
+
+// Persistent: each CTA (one per SM) takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// of the level's schedule (cum from k_oz_sched: each merge's tiles from its K).  The
+// pipeline's stage and accumulator barriers keep counting across tiles; the epilogue
+// re-zeroes the levels >= 6 after reading them and releases the accumulators (tfree)
+// before the next tile's first MMA.
 template <int S>
 __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restrict__ jobs,
                                                          const OzJob* __restrict__ ozj, int njobs,
@@ -368,31 +459,11 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::ST * C::STAGE);
-  // bars[0..ST) full, [ST..2ST) empty, 2ST accfull, 2ST+1 accempty, 2ST+2 done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::ST + 3);
+  // bars[0..ST) full, [ST..2ST) empty, 2ST accfull, 2ST+1 accempty, 2ST+2 done, 2ST+3 tfree
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::ST + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-  const JobView jv = job_of(cum, njobs);
-  const MergeJob J = jobs[jv.jb];
-  const OzJob* Z = ozj + jv.jb;
-  int* err = w.status + J.prob;
-  const MergeScalars Sc = w.scal[J.mid];
-  const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
-  const int m = J.n1 + J.n2;
-  const int nct = (m + kOzBN - 1) / kOzBN;
-  const int nrt1 = (J.n1 + kOzBM - 1) / kOzBM;
-  const int ct = (int)(jv.local % nct);
-  const int rtl = (int)(jv.local / nct);
-  if (ct * kOzBN >= K) return;                            // uniform: no barrier touched yet
-  const int h = rtl < nrt1 ? 0 : 1;
-  const int row0 = (h ? rtl - nrt1 : rtl) * kOzBM;        // within the half
-  const int rows_h = h ? J.n2 : J.n1;
-  const int rowbase = h ? J.n1 : 0;
-  const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
-  const int klen = h ? P3 + P2 : P1 + P3;
-  const int kb = h ? P1 : 0;
-  const int nst = klen / kOzBK;
-  const int nchunks = (nst + kOzChunk / kOzBK - 1) / (kOzChunk / kOzBK);
+  const int64_t total = cum[njobs];
+  if ((int64_t)blockIdx.x >= total) return;               // uniform: no barrier touched yet
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar0 = smem_u32(bars);
@@ -401,6 +472,8 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
   const uint32_t accfull = bar0 + 8u * (2 * C::ST);
   const uint32_t accempty = bar0 + 8u * (2 * C::ST + 1);
   const uint32_t done = bar0 + 8u * (2 * C::ST + 2);
+  const uint32_t tfree = bar0 + 8u * (2 * C::ST + 3);
+  int* err0 = w.status + jobs[find_job(cum, njobs, blockIdx.x)].prob;   // wait timeouts are reported here
 
   if (tid == 0) {
     for (int s = 0; s < C::ST; ++s) {
@@ -410,6 +483,7 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
     mbar_init(accfull, 1);
     mbar_init(accempty, kEpiWarps);
     mbar_init(done, 1);
+    mbar_init(tfree, kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -423,7 +497,8 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // Every accumulator starts at zero, so that every MMA may accumulate; the exact
-  // levels are restarted at each chunk by the one MMA that covers all of them.
+  // levels are restarted at each chunk by the one MMA that covers all of them, the
+  // others are re-zeroed by the epilogue after each tile.
   if (warp >= 2) {
     const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(((warp - 2) >> 2) * 32);
 #pragma unroll
@@ -435,82 +510,112 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
   tc_fence_after();
 
   if (warp == 0) {
-    if (lane == 0 && nst > 0) {
+    if (lane == 0) {
       // ---------------- TMA producer
-      const CUtensorMap* mA = &Z->mapA[h];
-      const CUtensorMap* mB = &Z->mapB;
-      asm volatile("prefetch.tensormap [%0];" ::"l"(mA) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(mB) : "memory");
-      int issued = 0;
-      for (int it = 0; it < nst; ++it) {
-        const int s = it % C::ST;
-        const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
-        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, err)) break;
-        const uint32_t sa = smem_u32(smem + s * C::STAGE);
-        mbar_expect_tx(full(s), C::STAGE);
-        tma_load_3d(sa, mA, full(s), it * kOzBK, row0, 0);
-        tma_load_3d(sa + C::A_BYTES, mB, full(s), kb + it * kOzBK, ct * kOzBN, 0);
-        issued = it + 1;
+      uint32_t g = 0, issued_total = 0;
+      for (int64_t t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        const OzTile T = oz_tile(jobs, cum, njobs, w, t);
+        int* err = w.status + jobs[T.jb].prob;
+        const CUtensorMap* mA = &ozj[T.jb].mapA[T.h];
+        const CUtensorMap* mB = &ozj[T.jb].mapB;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(mA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(mB) : "memory");
+        bool ok = true;
+        for (int it = 0; it < T.nst; ++it, ++g) {
+          const int s = (int)(g % C::ST);
+          const uint32_t ph = (g / C::ST) & 1u;
+          if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          mbar_expect_tx(full(s), C::STAGE);
+          tma_load_3d(sa, mA, full(s), it * kOzBK, T.row0, 0);
+          tma_load_3d(sa + C::A_BYTES, mB, full(s), T.kb + it * kOzBK, T.ct * kOzBN, 0);
+          issued_total = g + 1;
+        }
+        if (!ok) break;
       }
       if (*abort_flag) {      // let the copies in flight land before the CTA exits
         const long long t0 = global_ns();
-        for (int it = (issued > C::ST ? issued - C::ST : 0); it < issued; ++it) {
-          const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
-          while (!mbar_try(full(it % C::ST), ph) && global_ns() - t0 < kWaitNs) {
+        for (uint32_t q = (issued_total > (uint32_t)C::ST ? issued_total - C::ST : 0u); q < issued_total; ++q) {
+          const uint32_t ph = (q / C::ST) & 1u;
+          while (!mbar_try(full((int)(q % C::ST)), ph) && global_ns() - t0 < kWaitNs) {
           }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && nst > 0) {
+    if (lane == 0) {
       // ---------------- MMA issuer
       const int per_chunk = kOzChunk / kOzBK;
-      for (int it = 0; it < nst; ++it) {
-        const int s = it % C::ST;
-        const uint32_t ph = (uint32_t)(it / C::ST) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag, err)) break;
-        tc_fence_after();
-        const int chunk = it / per_chunk;
-        const bool first = (it % per_chunk) == 0;
-        const bool last = (it % per_chunk) == per_chunk - 1 || it == nst - 1;
-        const uint32_t sa = smem_u32(smem + s * C::STAGE);
-        const uint32_t sb = sa + C::A_BYTES;
-        bool ok = true;
+      uint32_t g = 0, cg = 0, ti = 0;
+      int* err = err0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const OzTile T = oz_tile(jobs, cum, njobs, w, t);
+        if (T.nst == 0) continue;
+        err = w.status + jobs[T.jb].prob;
+        if (ti > 0) {                                      // the previous tile's accumulators read and reset
+          if (!mbar_wait(tfree, (ti - 1) & 1u, abort_flag, err)) { ok = false; break; }
+          tc_fence_after();
+        }
+        for (int it = 0; it < T.nst; ++it, ++g) {
+          const int s = (int)(g % C::ST);
+          const uint32_t ph = (g / C::ST) & 1u;
+          if (!mbar_wait(full(s), ph, abort_flag, err)) { ok = false; break; }
+          tc_fence_after();
+          const int chunk = it / per_chunk;
+          const bool first = (it % per_chunk) == 0;
+          const bool last = (it % per_chunk) == per_chunk - 1 || it == T.nst - 1;
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < kOzBK / 16; ++kk) {
-          // groups whose levels are all >= 6 (accumulated over the whole k range)
+          for (int kk = 0; kk < kOzBK / 16; ++kk) {
+            // groups whose levels are all >= 6 (accumulated over the whole k range)
 #pragma unroll
-          for (int p = 1; p <= S; ++p) {
+            for (int p = 1; p <= S; ++p) {
 #pragma unroll
-            for (int qa = 1; qa <= 5; qa += 4) {
-              if (qa <= C::qmax(p) && p + qa >= 6) {
-                const int nq = C::qmax(p) - qa + 1 < 4 ? C::qmax(p) - qa + 1 : 4;
-                tc_mma(tmem + (uint32_t)((p + qa - 2) * kOzBN),
-                       sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
-                       sdesc(sb + (qa - 1) * (kOzBN * kOzBK * 2) + kk * 32), idesc_n(nq), 1u);
+              for (int qa = 1; qa <= 5; qa += 4) {
+                if (qa <= C::qmax(p) && p + qa >= 6) {
+                  const int nq = C::qmax(p) - qa + 1 < 4 ? C::qmax(p) - qa + 1 : 4;
+                  tc_mma(tmem + (uint32_t)((p + qa - 2) * kOzBN),
+                         sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                         sdesc(sb + (qa - 1) * (kOzBN * kOzBK * 2) + kk * 32), idesc_n(nq), 1u);
+                }
               }
             }
-          }
-          if (first && kk == 0 && chunk > 0) {
-            if (!mbar_wait(accempty, (uint32_t)(chunk - 1) & 1u, abort_flag, err)) { ok = false; break; }
-            tc_fence_after();
-          }
-          // groups that touch the exact levels 2..5; (p = 1, q = 1..4) comes first and
-          // overwrites all four at the start of a chunk
+            if (first && kk == 0 && chunk > 0) {           // the previous chunk's exact levels drained
+              if (!mbar_wait(accempty, (cg - 1) & 1u, abort_flag, err)) { ok = false; break; }
+              tc_fence_after();
+            }
+            // groups that touch the exact levels 2..5; (p = 1, q = 1..4) comes first and
+            // overwrites all four at the start of a chunk
 #pragma unroll
-          for (int p = 1; p <= 4; ++p) {
-            const int nq = C::qmax(p) < 4 ? C::qmax(p) : 4;
-            const uint32_t acc = (p == 1 && first && kk == 0) ? 0u : 1u;
-            tc_mma(tmem + (uint32_t)((p - 1) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
-                   sdesc(sb + kk * 32), idesc_n(nq), acc);
+            for (int p = 1; p <= 4; ++p) {
+              const int nq = C::qmax(p) < 4 ? C::qmax(p) : 4;
+              const uint32_t acc = (p == 1 && first && kk == 0) ? 0u : 1u;
+              tc_mma(tmem + (uint32_t)((p - 1) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                     sdesc(sb + kk * 32), idesc_n(nq), acc);
+            }
+          }
+          if (!ok) break;
+          tc_commit(empty(s));
+          if (last) {
+            tc_commit(accfull);
+            ++cg;
           }
         }
         if (!ok) break;
-        tc_commit(empty(s));
-        if (last) tc_commit(accfull);
+        tc_commit(done);
+        ++ti;
       }
-      tc_commit(done);
-      if (*abort_flag) mbar_wait(done, 0, abort_flag, err);
+      if (*abort_flag) {                                   // the MMAs issued complete before the exit
+        tc_commit(done);                                   // phases complete in order: the last
+        const long long t0 = global_ns();                  // committed tile's, then this one
+        if (ti > 0)
+          while (!mbar_try(done, (ti - 1) & 1u) && global_ns() - t0 < kWaitNs) {
+          }
+        while (!mbar_try(done, ti & 1u) && global_ns() - t0 < kWaitNs) {
+        }
+      }
     }
   } else {
     // ---------------- epilogue: warps 2..9; TMEM lane quadrant = warp % 4, and the
@@ -521,62 +626,75 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
     const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 32);
-    long long acc[32];
+    uint32_t cg = 0, ti = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+      const OzTile T = oz_tile(jobs, cum, njobs, w, t);
+      const MergeJob J = jobs[T.jb];
+      const OzJob* Z = ozj + T.jb;
+      int* err = w.status + J.prob;
+      long long acc[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const bool got = __all_sync(0xffffffffu, mbar_wait(accfull, (uint32_t)c & 1u, abort_flag, err));
-      if (!got) { ok = false; break; }
-      tc_fence_after();
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < T.nchunks; ++c) {
+        const bool got = __all_sync(0xffffffffu, mbar_wait(accfull, cg & 1u, abort_flag, err));
+        if (!got) { ok = false; break; }
+        tc_fence_after();
 #pragma unroll
-      for (int L = 2; L <= 5; ++L) {
-        uint32_t v[32];
-        tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
-        tmem_wait_ld();
+        for (int L = 2; L <= 5; ++L) {
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          acc[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
+          for (int j = 0; j < 32; ++j)
+            acc[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty);
+        ++cg;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(accempty);
-    }
-    if (ok && nst > 0) {
-      ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag, err));
-      tc_fence_after();
-    }
-    const int grow = row0 + row;
-    const bool rv = grow < rows_h;
-    if (ok) {
-      const double sig = rv ? Z->sigma[rowbase + grow] : 0.0;
-      double* const* outptr = w.outptr + J.v_off;
       // tail levels combined in FP32, smallest first: their rounding stays below the
       // FP32 accumulation error that level 6 already carries
       float tsum[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) tsum[j] = 0.0f;
-      if (nst > 0) {
+      if (ok && T.nst > 0) {
+        ok = __all_sync(0xffffffffu, mbar_wait(done, ti & 1u, abort_flag, err));
+        if (ok) {
+          tc_fence_after();
 #pragma unroll
-        for (int L = S + 2; L >= 6; --L) {
-          uint32_t v[32];
-          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
-          tmem_wait_ld();
-          const float wL = __int_as_float((127 - 8 * (L - 6)) << 23);     // 2^(-8 (L - 6))
+          for (int L = S + 2; L >= 6; --L) {
+            uint32_t v[32];
+            tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+            tmem_wait_ld();
+            const float wL = __int_as_float((127 - 8 * (L - 6)) << 23);     // 2^(-8 (L - 6))
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tsum[j] = fmaf(__uint_as_float(v[j]), wL, tsum[j]);
+            for (int j = 0; j < 32; ++j) tsum[j] = fmaf(__uint_as_float(v[j]), wL, tsum[j]);
+          }
+#pragma unroll
+          for (int L = 6; L <= S + 2; ++L) tmem_st32_zero(trow + (uint32_t)((L - 2) * kOzBN));
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tfree);
+          ++ti;
         }
       }
-      if (rv) {
+      if (!ok) break;
+      const int grow = T.row0 + row;
+      if (grow < T.rows_h) {
+        const double sig = Z->sigma[T.rowbase + grow];
+        double* const* outptr = w.outptr + J.v_off;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = ct * kOzBN + half * 32 + j;
-          if (col < K) {
+          const int col = T.ct * kOzBN + half * 32 + j;
+          if (col < T.K) {
             // acc counts level-5 units (2^-38), tsum level-6 units (2^-46)
             const double x = fma((double)tsum[j], 0x1p-8, (double)acc[j]);
             const int e = Z->texp[col] - 38;
             const double cs = e >= -1022 ? pow2(e) : ldexp(1.0, e);
-            outptr[col][rowbase + grow] = (x * cs) * sig;
+            outptr[col][T.rowbase + grow] = (x * cs) * sig;
           }
         }
       }
@@ -592,27 +710,41 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
 
 template <int S>
 void launch_s(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa, int64_t nb_sa,
-              const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t, int64_t ntiles, QBufs qb, DevWs w,
+              int64_t* cum_sb, int64_t nb_sb, int64_t* cum_t, int64_t ntiles, QBufs qb, DevWs w,
               cudaStream_t st) {
   using C = OzCfg<S>;
   // the shared-memory opt-in is a per-device attribute of the kernel: set it once on
-  // every device that launches it
+  // every device that launches it (with the device's SM count for the persistent grid)
   static std::mutex mu;
   static bool attr[64] = {};
+  static int sms[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
+  int nsm = 148;
   {
     std::lock_guard<std::mutex> g(mu);
     if (dev < 0 || dev >= 64 || !attr[dev]) {
       cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-      if (dev >= 0 && dev < 64) attr[dev] = true;
+      int n = 0;
+      if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+      if (dev >= 0 && dev < 64) {
+        attr[dev] = true;
+        sms[dev] = n;
+      }
+      nsm = n;
+    } else {
+      nsm = sms[dev];
     }
   }
+  // nb_sb and ntiles are the host's bounds (K = m); the kernels stride over the
+  // schedules k_oz_sched writes from the actual K
   if (part == 0) {
+    k_oz_sched<<<1, 1024, 0, st>>>(jobs, njobs, w.scal, cum_sb, cum_t);
     if (nb_sa) k_oz_slice_a<S><<<(unsigned)nb_sa, 256, 0, st>>>(jobs, ozj, njobs, cum_sa, w);
-    if (nb_sb) k_oz_slice_b<S><<<(unsigned)nb_sb, 256, 0, st>>>(jobs, ozj, njobs, cum_sb, w);
+    if (nb_sb) k_oz_slice_b<S><<<grid_cap(nb_sb, 8), 256, 0, st>>>(jobs, ozj, njobs, cum_sb, w);
   } else if (ntiles) {
-    k_oz_gemm<S><<<(unsigned)ntiles, kThreads, C::SMEM, st>>>(jobs, ozj, njobs, cum_t, qb, w);
+    const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    k_oz_gemm<S><<<grid, kThreads, C::SMEM, st>>>(jobs, ozj, njobs, cum_t, qb, w);
   }
 }
 
@@ -687,7 +819,7 @@ int64_t oz_tiles(const MergeJob& J) {
 }
 
 void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
-                        int64_t nb_sa, const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t,
+                        int64_t nb_sa, int64_t* cum_sb, int64_t nb_sb, int64_t* cum_t,
                         int64_t ntiles, int slices, QBufs qb, DevWs w, cudaStream_t st) {
   switch (slices) {
     case 5: launch_s<5>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;

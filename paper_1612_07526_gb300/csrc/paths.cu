@@ -172,8 +172,8 @@ int launch_product(const PathPlan& pp, int l, const tdc_opts& o, const std::vect
   if (L && L->oz) {
     const OzJob* z = reinterpret_cast<const OzJob*>(pp.table_dev + L->tab_off);
     const int64_t* c0 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[0]);
-    const int64_t* c1 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[1]);
-    const int64_t* c2 = reinterpret_cast<const int64_t*>(pp.table_dev + L->cum_off[2]);
+    int64_t* c1 = reinterpret_cast<int64_t*>(pp.table_dev + L->cum_off[1]);
+    int64_t* c2 = reinterpret_cast<int64_t*>(pp.table_dev + L->cum_off[2]);
     phase_mark(9, true, 0, st);
     launch_ozaki_level(0, jobs, z, (int)hjobs.size(), c0, L->nb[0], c1, L->nb[1], c2, L->nb[2], pp.slices, qb,
                        w, st);

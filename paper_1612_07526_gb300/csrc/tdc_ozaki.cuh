@@ -48,10 +48,11 @@ struct OzJob {                      // CUtensorMap members force 64+ byte alignm
 size_t oz_job_bytes(const MergeJob& J, int slices);
 bool oz_fill_job(OzJob& z, const MergeJob& J, unsigned char* base, int slices);
 
-// Launches, for one level's merges, the slicing kernels (part 0) or the tcgen05
-// GEMM (part 1).
+// Launches, for one level's merges, the schedule and slicing kernels (part 0) or the
+// persistent tcgen05 GEMM (part 1).  cum_sb and cum_t are rewritten on the device from
+// the merges' K; nb_sb and ntiles are host bounds (K = m) that size the grids.
 void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int njobs, const int64_t* cum_sa,
-                        int64_t nb_sa, const int64_t* cum_sb, int64_t nb_sb, const int64_t* cum_t,
+                        int64_t nb_sa, int64_t* cum_sb, int64_t nb_sb, int64_t* cum_t,
                         int64_t ntiles, int slices, QBufs qb, DevWs w, cudaStream_t st);
 // bf16 slice products per FP64-equivalent product: pairs (p, q) with p + q <= S + 2.
 int oz_slice_pairs(int slices);
