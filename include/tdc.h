@@ -440,6 +440,19 @@ int tdc_diag_reciprocal(const double* x, double* r, int64_t n, void* stream);
 int tdc_diag_rsqrt(const double* x, double* r, int64_t n, void* stream);
 
 /*
+ * tdc_diag_split_combine -- diagnostic: r[i] = (acc[i] + tsum[i] 2^-8) 2^e2[i] as the
+ * split-precision product's epilogue forms each output from its exact integer levels
+ * (acc, in level-5 units) and its FP32 tail levels (tsum, in level-6 units) (Eq. (6)'s
+ * product, split form): acc and tsum 2^-8 converted to doubles exactly (acc rounded to
+ * nearest when |acc| > 2^53), one FP64 addition, then the power-of-two scaling, exact
+ * when the result is a normal double.  acc: n device int64, tsum: n device floats,
+ * e2: n device int32, r: n device doubles.  Asynchronous on `stream`.  Returns 0, -i
+ * for a bad argument i, or 4 for a launch error.
+ */
+int tdc_diag_split_combine(const int64_t* acc, const float* tsum, const int32_t* e2, double* r, int64_t n,
+                           void* stream);
+
+/*
  * tdc_diag_wait_timeout -- diagnostic of the bounded device waits: runs the split-
  * precision product's mbarrier wait (the one its producer, MMA and epilogue roles use)
  * on a barrier that nothing arrives on, with a limit of limit_ns nanoseconds.  The

@@ -117,6 +117,7 @@ SIGNATURES = [
     ("tdc_diag_reciprocal", ctypes.c_int, [_P, _P, _I64, _P]),
     ("tdc_diag_rsqrt", ctypes.c_int, [_P, _P, _I64, _P]),
     ("tdc_diag_wait_timeout", ctypes.c_int, [_I64, _P, _P, _P]),
+    ("tdc_diag_split_combine", ctypes.c_int, [_P, _P, _P, _P, _I64, _P]),
 ]
 
 

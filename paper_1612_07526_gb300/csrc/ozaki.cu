@@ -128,11 +128,11 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
   }
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
-                                            int y, int z) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y, int z, int v) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-      ::"r"(dst), "l"(map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
+      ::"r"(dst), "l"(map), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(v)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -188,6 +188,56 @@ __device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // 2^e for e in the normal range, built from its bit pattern (exact).
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// The epilogue's conversions and power-of-two scalings on the integer pipes, from the
+// IEEE-754 binary64/binary32 formats (GB300's FP64 pipe issues 2 lanes per clock per SM,
+// and with five FP64 operations per output it, not the tensor pipe, bounded the GEMM).
+// The int64 value v as the nearest double (ties to even): sign, the leading bit's
+// position p, and the 52 bits after it, rounded when p > 52.
+__device__ __forceinline__ double i64_to_double_bits(long long v) {
+  if (v == 0) return 0.0;
+  const unsigned long long s = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int p = 63 - __clzll((long long)u);
+  unsigned long long q;
+  if (p <= 52) {
+    q = u << (52 - p);
+  } else {
+    const int sh = p - 52;
+    q = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    if (q >> 53) {                                       // rounded up to the next power of two
+      q >>= 1;
+      ++p;
+    }
+  }
+  return __longlong_as_double((long long)(s | ((unsigned long long)(1023 + p) << 52) | (q & 0xFFFFFFFFFFFFFull)));
+}
+// f 2^e exactly as a double, for a normal float f and a result in the normal range
+// (the exponent field rebased, the 23 fraction bits moved up); other f through FP64.
+__device__ __forceinline__ double f32_pow2_to_double(float f, int e) {
+  const unsigned b = __float_as_uint(f);
+  const int ex = (int)((b >> 23) & 0xFFu);
+  if (ex == 0 || ex == 0xFF) return ldexp((double)f, e);  // zero, subnormal, inf, NaN
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)(ex - 127 + 1023 + e) << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+// x 2^e exactly when the result stays normal (the exponent field moved by e), else
+// through ldexp.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int ne = ex + e;
+  if (ex != 0 && ex != 0x7FF && ne >= 1 && ne <= 2046) return __longlong_as_double(b + ((long long)e << 52));
+  return ldexp(x, e);
+}
+// One output of the product: (acc + tsum 2^-8) 2^e, acc in level-5 units, tsum in
+// level-6 units; one FP64 addition.
+__device__ __forceinline__ double oz_combine(long long acc, float tsum, int e) {
+  return scale_pow2(i64_to_double_bits(acc) + f32_pow2_to_double(tsum, -8), e);
+}
 
 struct JobView {
   int jb;
@@ -281,7 +331,9 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
         v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
         v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
         v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
-        *reinterpret_cast<uint4*>(abase + ((int64_t)p * rows_h + r0 + wr) * Z.ldk + k0 + wk) = v;
+        const int k = k0 + wk;                 // k-blocked: [slice][k / 32][row][k % 32]
+        *reinterpret_cast<uint4*>(abase + (((int64_t)p * (Z.ldk / kOzBK) + k / kOzBK) * rows_h + r0 + wr) * kOzBK +
+                                  (k % kOzBK)) = v;
       }
     }
     __syncthreads();
@@ -339,7 +391,8 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
       vv.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
       vv.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
       vv.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
-      *reinterpret_cast<uint4*>(Z.b + ((int64_t)p * m + i) * Z.ldk + k0) = vv;
+      *reinterpret_cast<uint4*>(Z.b + (((int64_t)p * (Z.ldk / kOzBK) + k0 / kOzBK) * m + i) * kOzBK +
+                                (k0 % kOzBK)) = vv;
     }
   }
 }
@@ -527,8 +580,8 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
           if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
           const uint32_t sa = smem_u32(smem + s * C::STAGE);
           mbar_expect_tx(full(s), C::STAGE);
-          tma_load_3d(sa, mA, full(s), it * kOzBK, T.row0, 0);
-          tma_load_3d(sa + C::A_BYTES, mB, full(s), T.kb + it * kOzBK, T.ct * kOzBN, 0);
+          tma_load_4d(sa, mA, full(s), 0, T.row0, it, 0);
+          tma_load_4d(sa + C::A_BYTES, mB, full(s), 0, T.ct * kOzBN, T.kb / kOzBK + it, 0);
           issued_total = g + 1;
         }
         if (!ok) break;
@@ -684,17 +737,17 @@ __global__ __launch_bounds__(kThreads, 1) void k_oz_gemm(const MergeJob* __restr
       if (!ok) break;
       const int grow = T.row0 + row;
       if (grow < T.rows_h) {
-        const double sig = Z->sigma[T.rowbase + grow];
+        // sigma is a power of two (or zero: a row with no entries in its k range)
+        const long long sb = __double_as_longlong(Z->sigma[T.rowbase + grow]);
+        const bool zrow = (sb & 0x7FFFFFFFFFFFFFFFll) == 0;
+        const int es = (int)((sb >> 52) & 0x7FF) - 1023;
         double* const* outptr = w.outptr + J.v_off;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = T.ct * kOzBN + half * 32 + j;
           if (col < T.K) {
-            // acc counts level-5 units (2^-38), tsum level-6 units (2^-46)
-            const double x = fma((double)tsum[j], 0x1p-8, (double)acc[j]);
-            const int e = Z->texp[col] - 38;
-            const double cs = e >= -1022 ? pow2(e) : ldexp(1.0, e);
-            outptr[col][T.rowbase + grow] = (x * cs) * sig;
+            // acc counts level-5 units (2^-38), tsum level-6 units (2^-46); times tau_i sigma_r
+            outptr[col][T.rowbase + grow] = zrow ? 0.0 : oz_combine(acc[j], tsum[j], Z->texp[col] - 38 + es);
           }
         }
       }
@@ -761,14 +814,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-bool encode3d(CUtensorMap* map, void* base, int64_t ldk, int64_t rows, int slices, int box_rows) {
+// Slices in k-blocked order, [slice][k / 32][row][k % 32]: a tile's box (32 k, its rows,
+// one k block, every slice) is one contiguous run of rows x 64 bytes per slice, and
+// lands in shared memory as [slice][row][32 k], as the MMA descriptors expect.
+bool encode4d(CUtensorMap* map, void* base, int64_t ldk, int64_t rows, int slices, int box_rows) {
   auto fn = encoder();
   if (!fn) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)slices};
-  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(ldk * rows * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)slices};
-  cuuint32_t es[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const int64_t nkb = ldk / kOzBK;
+  cuuint64_t dims[4] = {(cuuint64_t)kOzBK, (cuuint64_t)rows, (cuuint64_t)nkb, (cuuint64_t)slices};
+  cuuint64_t strides[3] = {(cuuint64_t)kOzBK * 2, (cuuint64_t)(rows * kOzBK * 2), (cuuint64_t)(nkb * rows * kOzBK * 2)};
+  cuuint32_t box[4] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, 1u, (cuuint32_t)slices};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -803,9 +860,9 @@ bool oz_fill_job(OzJob& z, const MergeJob& J, unsigned char* base, int slices) {
   z.texp = reinterpret_cast<int32_t*>(base + off);
   z.ldk = ldk;
   z.slices = slices;
-  bool ok = encode3d(&z.mapA[0], z.a[0], ldk, J.n1, slices, kOzBM);
-  ok = ok && encode3d(&z.mapA[1], z.a[1], ldk, J.n2, slices, kOzBM);
-  ok = ok && encode3d(&z.mapB, z.b, ldk, m, slices, kOzBN);
+  bool ok = encode4d(&z.mapA[0], z.a[0], ldk, J.n1, slices, kOzBM);
+  ok = ok && encode4d(&z.mapA[1], z.a[1], ldk, J.n2, slices, kOzBM);
+  ok = ok && encode4d(&z.mapB, z.b, ldk, m, slices, kOzBN);
   return ok;
 }
 
@@ -838,6 +895,13 @@ int oz_slice_pairs(int slices) {
 
 namespace tdc {
 namespace {
+// The product epilogue's combination of one output (integer-pipe conversions, one FP64
+// addition), element by element.
+__global__ void k_diag_combine(const long long* __restrict__ acc, const float* __restrict__ ts,
+                               const int* __restrict__ e, double* __restrict__ r, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = oz_combine(acc[i], ts[i], e[i]);
+}
 // The product kernel's bounded wait, on an mbarrier that nothing arrives on: after
 // limit_ns it sets the abort flag and ST_WAIT in *err and returns (no copy or MMA is
 // in flight, no tensor memory is held).  out[0] = 1 if the wait ended by itself.
@@ -860,5 +924,18 @@ extern "C" int tdc_diag_wait_timeout(int64_t limit_ns, int* dev_status, int* dev
   if (!dev_status) return -2;
   if (!dev_out) return -3;
   tdc::k_diag_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>((long long)limit_ns, dev_status, dev_out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int tdc_diag_split_combine(const int64_t* acc, const float* tsum, const int32_t* e2, double* r, int64_t n,
+                                      void* stream) {
+  if (n < 0) return -5;
+  if (n == 0) return 0;
+  if (!acc) return -1;
+  if (!tsum) return -2;
+  if (!e2) return -3;
+  if (!r) return -4;
+  tdc::k_diag_combine<<<tdc::grid_cap((n + 255) / 256, 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const long long*>(acc), tsum, e2, r, n);
   return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }

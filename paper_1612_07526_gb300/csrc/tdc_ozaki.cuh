@@ -34,8 +34,8 @@ constexpr int kOzPad = 64;          // padding of the Gu groups in the k coordin
 struct OzJob {                      // CUtensorMap members force 64+ byte alignment
   CUtensorMap mapA[2];              // A slices of the T1 rows (0) and T2 rows (1)
   CUtensorMap mapB;                 // B slices (columns of Qhat)
-  uint16_t* a[2];                   // a[h] + ((p * rows_h) + r) * ldk + k
-  uint16_t* b;                      // b + ((q * m) + i) * ldk + k
+  uint16_t* a[2];                   // a[h] + ((p * ldk / 32 + k / 32) * rows_h + r) * 32 + k % 32
+  uint16_t* b;                      // b + ((q * ldk / 32 + k / 32) * m + i) * 32 + k % 32
   double* sigma;                    // per merge-local row: power-of-two row scale
   int32_t* texp;                    // per column: tau_i = 2^texp
   int64_t ldk;                      // padded k extent

@@ -79,6 +79,9 @@ def test_host_side_argument_checks(lib):
     assert lib.tdc_diag_reciprocal(None, None, -1, None) == -3
     assert lib.tdc_diag_rsqrt(None, None, -1, None) == -3
     assert lib.tdc_diag_rsqrt(None, P(8), 4, None) == -1
+    assert lib.tdc_diag_split_combine(P(8), P(8), P(8), P(8), -1, None) == -5
+    assert lib.tdc_diag_split_combine(None, P(8), P(8), P(8), 4, None) == -1
+    assert lib.tdc_diag_split_combine(P(8), P(8), P(8), None, 4, None) == -4
     assert lib.tdc_workspace_bytes(0, ctypes.byref(o)) == 0
     assert lib.tdc_workspace_bytes(1024, ctypes.byref(o)) > 2 * 1024 * 1024 * 8
 
