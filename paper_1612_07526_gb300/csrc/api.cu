@@ -268,7 +268,7 @@ static Layout carve(void* ws, int64_t nvec, int64_t qwords, int64_t nmerges, int
   w.tlo = c.take<int32_t>(N);
   w.thi = c.take<int32_t>(N);
   w.scal = c.take<MergeScalars>((size_t)std::max<int64_t>(nmerges, 1));
-  w.lroots = c.take<unsigned long long>(kMaxLevels);
+  w.lroots = c.take<unsigned long long>(2 * kMaxLevels);
   const size_t NL = (size_t)std::max<int64_t>(nleaf, 1);
   w.lrot = c.take<double2>(NL * kLeafRot);
   w.lroti = c.take<uint8_t>(NL * kLeafRot);
@@ -322,7 +322,7 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L_in, const
   L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   // leaves of one element and n < 2^31 give at most 31 merge levels
   static_assert(kMaxLevels >= 32, "level table too small");
-  cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.lroots, 0, 2 * kMaxLevels * sizeof(unsigned long long), st);
   cudaMemsetAsync(L.w.scal, 0, std::max<int64_t>(P.nmerges, 1) * sizeof(MergeScalars), st);
   phase_mark(0, true, 0, st);
   launch_tear(P_<int64_t>(L, P.o_tlist), P_<int64_t>(L, P.o_tptr), nprob, (int64_t)P.tear_list.size(),
@@ -857,7 +857,7 @@ static int merge_core(int64_t n1, int64_t n2, const double* D, const double* Q, 
   L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   const LevelPlan& lv = P.levels[0];
   const MergeJob* jobs = P_<MergeJob>(L, lv.o_jobs);
-  cudaMemsetAsync(L.w.lroots, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.lroots, 0, 2 * kMaxLevels * sizeof(unsigned long long), st);
   cudaMemsetAsync(L.w.scal, 0, sizeof(MergeScalars), st);
   launch_merge_level(0, jobs, 1, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                      lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lambda, nullptr,
@@ -1141,7 +1141,7 @@ int tdc_batched_plan_execute_persistent(const tdc_batched_plan* h, const double*
   L.w.ext = h->o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   const Plan& P = h->P;
   cudaMemsetAsync(L.w.status, 0, sizeof(int) * h->batch, st);
-  cudaMemsetAsync(L.w.lroots, 0, kMaxLevels * sizeof(unsigned long long), st);
+  cudaMemsetAsync(L.w.lroots, 0, 2 * kMaxLevels * sizeof(unsigned long long), st);
   cudaMemsetAsync(L.w.scal, 0, std::max<int64_t>(P.nmerges, 1) * sizeof(MergeScalars), st);
   cudaMemsetAsync(L.queue, 0, sizeof(unsigned), st);
   QBufs qb{Q_cat, L.pool, nullptr};

@@ -108,7 +108,8 @@ struct DevWs {
   int32_t *chain;             // first rotation of each chain
   double *rc, *rs;
   MergeScalars *scal;         // per merge id
-  unsigned long long *lroots; // per tree level: non-deflated roots of the level's merges (kMaxLevels)
+  unsigned long long *lroots; // per tree level: non-deflated roots of the level's merges, then (at
+                              // kMaxLevels + level) the level's largest K (2 kMaxLevels)
   double *dmod;               // torn diagonal (Eq. 2 corner updates)
   double2 *lrot;              // leaf QL: recorded plane rotations (c, s), kLeafRot per leaf
   uint8_t *lroti;             // leaf QL: row index i of each rotation (rows i, i+1)
