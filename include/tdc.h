@@ -96,6 +96,11 @@ size_t tdc_workspace_bytes(int64_t n, const tdc_opts* opts);
  *   opts     NULL for defaults
  *   ws       device workspace of at least tdc_workspace_bytes(n, opts) bytes,
  *            256-byte aligned
+ * Scale: the entries are used as given (no internal rescaling).  The Loewner products
+ * multiply differences of eigenvalues four at a time and the secular solver's FP32
+ * phase holds d in FP32, so max |T| should lie in [2^-120, 2^120]; outside it, scale
+ * d and e by a power of two first (exact: the eigenvalues scale by it, the
+ * eigenvectors are unchanged).
  */
 int tdc_syev_tridiag(int64_t n, const double* d, const double* e, double* lambda,
                      double* Q, int64_t ldq, const tdc_opts* opts, void* ws,

@@ -32,7 +32,7 @@ struct PathPlan {
 };
 
 // Merges of order below this use the FP64 product even on the split path.
-constexpr int64_t kOzMinOrder = 1024;
+constexpr int64_t kOzMinOrder = 256;
 
 bool path_supported(const tdc_opts& o);
 // Decides the product form per level and sizes its workspace (no device access).
