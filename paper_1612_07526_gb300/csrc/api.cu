@@ -315,9 +315,36 @@ static std::vector<const std::vector<MergeJob>*> level_jobs(const Plan& P) {
   return v;
 }
 
+// A second stream and two events per host thread and device, for running the top
+// merges' deflated-column copy beside their Loewner, norm and product kernels (created on
+// first use; never released while the thread lives).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream* side_stream() {
+  static thread_local SideStream r[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  SideStream& x = r[dev];
+  if (!x.s) {
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess) {
+      x.s = nullptr;
+      return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(x.s);
+      x.s = nullptr;
+      return nullptr;
+    }
+  }
+  return &x;
+}
+
 static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L_in, const tdc_opts& o,
                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
-                    bool sign_norm, double* qa_for_sign, cudaStream_t st) {
+                    bool sign_norm, double* qa_for_sign, cudaStream_t st, bool overlap = true) {
   Layout L = L_in;
   L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   // leaves of one element and n < 2^31 give at most 31 merge levels
@@ -341,15 +368,32 @@ static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L_in, const
       any_fin |= J.fin != 0;
       maxm = std::max<int64_t>(maxm, J.n1 + J.n2);
     }
+    // Deflated columns move only in a problem's top merge (below, the slot table keeps
+    // them in place).  Their copy needs the placement only, and touches none of the
+    // columns the Loewner, norm and product kernels read or write, so it runs beside
+    // them on a side stream (HBM-bound beside FP64- or tensor-bound work); the sign
+    // convention waits for both.
+    SideStream* side = (any_fin && overlap) ? side_stream() : nullptr;
     launch_merge_level((int)li, jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_crows),
                        lv.crows.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(), lam, e, qb, L.w,
-                       o.max_secular_iter, o.secular_lanes, merge_cta_threads(maxm), st);
+                       o.max_secular_iter, o.secular_lanes, merge_cta_threads(maxm), st,
+                       side ? side->fork : nullptr);
+    if (side) {
+      cudaStreamWaitEvent(side->s, side->fork, 0);
+      launch_defl_copy_cols(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
+                            lv.ccols.back(), maxm, qb, L.w, side->s);
+      cudaEventRecord(side->join, side->s);
+    }
     const int prc = launch_product(pp, (int)li, o, lv.jobs, jobs, PM_<int64_t>(L, lv.o_ctiles), qb, L.w, st);
+    if (side) cudaStreamWaitEvent(st, side->join, 0);
     if (prc) return prc;
-    // deflated columns move only in a problem's top merge; below, the slot table keeps them in place
-    if (any_fin)
-      launch_defl_copy(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
-                       lv.ccols.back(), maxm, qb, L.w, sign_norm && any_root, st);
+    if (any_fin) {
+      if (!side)
+        launch_defl_copy_cols(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols),
+                              lv.ccols.back(), maxm, qb, L.w, st);
+      launch_sign(jobs, nj, P_<int64_t>(L, lv.o_cw8), lv.cw8.back(), P_<int64_t>(L, lv.o_ccols), lv.ccols.back(),
+                  maxm, qb, L.w, sign_norm && any_root, st);
+    }
   }
   (void)qa_for_sign;
   return 0;
@@ -585,7 +629,7 @@ int syev_core(int64_t n, const double* d, const double* e, double* lambda, doubl
   cudaMemcpyAsync(L.plan, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice, st);
   if (!path_bind(pp, L.arena, L.table, lj, st)) return 4;
   QBufs qb{Q, L.pool, nullptr};
-  const int prc = run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st);
+  const int prc = run_plan(P, pp, L, o, d, e ? e : d, lambda, qb, n, 1, true, Q, st, profile_accounting);
   if (prc) return prc;
   if (profile_accounting) prof_account(P, pp, L.w.scal, st);
   return launch_status();

@@ -341,8 +341,9 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
 }
 
 // ------------------------------------------------------------------------ generated, sliced Qhat
-// Blocks strided over the level's schedule (cum from k_oz_sched): column i < K of
-// Qhat, k range [2048 kc, 2048 kc + 2048) of its padded length KP.
+// Blocks strided over the level's schedule (cum from k_oz_sched): a merge's K x KP
+// entries of Qhat (KP its padded length) as K KP / 8 vectors of 8 k, 256 vectors per
+// block, thread f of the merge taking column f / (KP / 8) and k from 8 (f % (KP / 8)).
 template <int S>
 __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__ jobs,
                                                     const OzJob* __restrict__ ozj, int njobs,
@@ -350,33 +351,33 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
   const int64_t total = cum[njobs];
   for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int jb = find_job(cum, njobs, vb);
-    const int64_t local = vb - cum[jb];
     const MergeJob J = jobs[jb];
-    const OzJob& Z = ozj[jb];
-    const int m = J.n1 + J.n2;
     const MergeScalars Sc = w.scal[J.mid];
     const int K = Sc.K, c1 = Sc.c1, c3 = Sc.c3;
     const int P1 = (int)rup(c1, kOzPad), P3 = (int)rup(c3, kOzPad), P2 = (int)rup(K - c1 - c3, kOzPad);
-    const int KP = P1 + P3 + P2;
-    const int64_t nkc = (KP + 2047) / 2048;
-    const int i = (int)(local / nkc);
-    const int kc = (int)(local % nkc);
+    const int KP = P1 + P3 + P2, nv = KP / 8;
+    const int64_t f = (vb - cum[jb]) * 256 + threadIdx.x;
+    if (f >= (int64_t)K * nv) continue;
+    const int i = (int)(f / nv);
+    const int k0 = (int)(f % nv) * 8;
+    const OzJob& Z = ozj[jb];
+    const int m = J.n1 + J.n2;
     const int64_t o = J.v_off;
     const int32_t* __restrict__ kperm = w.kperm + o;
     const double* __restrict__ wcol = w.wptr[o + i];     // unscaled column i of the Cauchy factor
     const double si = w.sinv[o + i];
+    // tau_i = 2^e >= the column's largest entry: e from the exponent field (cmax normal), else frexp
+    const long long cb = __double_as_longlong(w.cmax[o + i]);
+    const int ce = (int)((cb >> 52) & 0x7FF);
     int e = 0;
-    const double cm = w.cmax[o + i];
-    if (cm > 0.0) frexp(cm, &e);
-    if (kc == 0 && threadIdx.x == 0) Z.texp[i] = e;
+    if (ce != 0 && ce != 0x7FF && cb > 0) e = ce - 1022;
+    else if (cb > 0) frexp(w.cmax[o + i], &e);
+    if (k0 == 0) Z.texp[i] = e;
     const int shift = 8 * S - 1 - e;
-    const int k0 = kc * 2048 + threadIdx.x * 8;
-    if (k0 >= KP) continue;
     uint16_t dg[8][S];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int k = k0 + j;
-      const int kg = padded_to_grouped(k, c1, c3, K, P1, P3);
+      const int kg = padded_to_grouped(k0 + j, c1, c3, K, P1, P3);
       double v = 0.0;
       if (kg >= 0) v = wcol[kperm[kg]] * si;
       uint16_t tt[S];
@@ -398,7 +399,7 @@ __global__ __launch_bounds__(256) void k_oz_slice_b(const MergeJob* __restrict__
 }
 
 // The level's schedules from the merges' K (known only on the device): blocks of
-// k_oz_slice_b (K columns x cdiv(KP, 2048)) and tiles of k_oz_gemm ((row tiles of T1
+// k_oz_slice_b (cdiv(K KP / 8, 256)) and tiles of k_oz_gemm ((row tiles of T1
 // + of T2) x cdiv(K, kOzBN)); cum[j] = units of the merges before j.  One block of
 // 1024 threads, each summing a contiguous run of merges, then a scan.
 __global__ __launch_bounds__(1024) void k_oz_sched(const MergeJob* __restrict__ jobs, int njobs,
@@ -413,7 +414,7 @@ __global__ __launch_bounds__(1024) void k_oz_sched(const MergeJob* __restrict__ 
     const MergeScalars& Sc = scal[J.mid];
     const int K = Sc.K;
     const int64_t KP = rup(Sc.c1, kOzPad) + rup(Sc.c3, kOzPad) + rup(K - Sc.c1 - Sc.c3, kOzPad);
-    sb = (int64_t)K * ((KP + 2047) / 2048);
+    sb = ((int64_t)K * (KP / 8) + 255) / 256;
     tl = (int64_t)((J.n1 + kOzBM - 1) / kOzBM + (J.n2 + kOzBM - 1) / kOzBM) * ((K + kOzBN - 1) / kOzBN);
   };
   int64_t a = 0, b = 0;

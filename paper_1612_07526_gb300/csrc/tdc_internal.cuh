@@ -226,7 +226,7 @@ int merge_cta_threads(int64_t maxm);
 void launch_merge_level(int lev, const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                         const int64_t* cum_rows, int64_t nb_rows, const int64_t* cum_cols,
                         int64_t nb_cols, double* lam, const double* e, QBufs qb, DevWs w,
-                        int max_iter, int sec_lanes, int cta, cudaStream_t st);
+                        int max_iter, int sec_lanes, int cta, cudaStream_t st, cudaEvent_t placed = nullptr);
 // FP64 product, tile shape `cfg` (0 .. kGemmShapes-1): 128x128, 128x64, 64x64, 64x32,
 // 32x32, 128x32, 64x16, 128x16, 16x16, 16x32, 16x64, 32x16 (rows x columns).
 // cum_tiles (njobs + 1 entries of device memory) is rewritten with the
@@ -243,6 +243,13 @@ constexpr int64_t kWideColumn = 2048;
 void launch_defl_copy(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
                       const int64_t* cum_cols, int64_t nb_cols, int64_t maxm, QBufs qb, DevWs w,
                       bool any_root, cudaStream_t st);
+// The same in two parts: the deflated columns' copy, and the sign convention of the
+// problems' top merges (which needs the product's columns too).
+void launch_defl_copy_cols(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8,
+                           const int64_t* cum_cols, int64_t nb_cols, int64_t maxm, QBufs qb, DevWs w,
+                           cudaStream_t st);
+void launch_sign(const MergeJob* jobs, int njobs, const int64_t* cum_w8, int64_t nb_w8, const int64_t* cum_cols,
+                 int64_t nb_cols, int64_t maxm, QBufs qb, DevWs w, bool any_root, cudaStream_t st);
 
 
 constexpr int kGemmShapes = 12;
