@@ -342,9 +342,12 @@ static SideStream* side_stream() {
   return &x;
 }
 
+static bool phases_profiled();   // per-phase event timing on (the phases then run one after another)
+
 static int run_plan(const Plan& P, const PathPlan& pp, const Layout& L_in, const tdc_opts& o,
                     const double* d, const double* e, double* lam, QBufs qb, int64_t nvec, int nprob,
                     bool sign_norm, double* qa_for_sign, cudaStream_t st, bool overlap = true) {
+  if (phases_profiled()) overlap = false;
   Layout L = L_in;
   L.w.ext = o.eigvec == TDC_EIGVEC_EXTENDED ? 1 : 0;
   // leaves of one element and n < 2^31 give at most 31 merge levels
@@ -497,6 +500,7 @@ static ProfState g_prof;
 // marks on their thread for their duration.
 static thread_local bool t_prof_suspended = false;
 ProfileSuspend::ProfileSuspend(bool on) : prev_(t_prof_suspended) { t_prof_suspended = prev_ || on; }
+static bool phases_profiled() { return g_prof.on && !t_prof_suspended; }
 ProfileSuspend::~ProfileSuspend() { t_prof_suspended = prev_; }
 
 

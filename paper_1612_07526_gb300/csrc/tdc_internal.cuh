@@ -157,8 +157,15 @@ __device__ __forceinline__ int pool_index(const MergeJob& J, const QBufs& qb, co
   const double* base = qb.P + J.pool_off + J.lo;
   if (p < base) return -1;
   const int64_t d = p - base;
-  if (d % J.pn != 0 || d / J.pn >= 3 * (int64_t)J.pn) return -1;
-  return (int)(d / J.pn);
+  // d / pn without a 64-bit division: a float estimate (d < 3 pn^2 < 2^63, so it is off
+  // by at most one), corrected with integer products
+  const int64_t pn = J.pn;
+  if (d >= 3 * pn * pn) return -1;
+  int64_t q = (int64_t)((float)d * (1.0f / (float)pn));
+  if (q * pn > d) --q;
+  else if ((q + 1) * pn <= d) ++q;
+  if (q < 0 || q * pn != d || q >= 3 * pn) return -1;
+  return (int)q;
 }
 
 // Smallest j with cum[j+1] > b (cum has njobs+1 entries, cum[0] = 0).
