@@ -393,8 +393,22 @@ def backward_measurement(api, _lib, lib, torch, batch=64, n=4096, m=64):
     b1.record()
     b1.synchronize()
     bw_ms = b0.elapsed_time(b1) / reps
+    # the same backward with its two products on the split-precision tensor-core path
+    so = {"path": PATHS["ozaki"]}
+    gd_s, ge_s = api.syev_backward_batched(sizes, lam, q, w, gq, max_cols=m, opts=so)
+    torch.cuda.synchronize()
+    b0.record()
+    for _ in range(reps):
+        gd_s, ge_s = api.syev_backward_batched(sizes, lam, q, w, gq, max_cols=m, opts=so)
+    b1.record()
+    b1.synchronize()
+    bw_split_ms = b0.elapsed_time(b1) / reps
+    gscale = max(torch.max(torch.abs(gd)).item(), torch.max(torch.abs(ge)).item())
+    split_err = max(torch.max(torch.abs(gd_s - gd)).item(), torch.max(torch.abs(ge_s - ge)).item()) / gscale
     flops = batch * (4.0 * n * n * m + 6.0 * n * n)
     out = {"forward_ms": fwd_ms, "backward_ms": bw_ms, "problems": batch, "n": n, "loss_columns": m,
+           "backward_split_products_ms": bw_split_ms,
+           "backward_split_max_rel_diff_vs_fp64": split_err,
            "backward_algorithmic_flops": flops,
            "backward_fp64_tflops": flops / (bw_ms * 1e-3) / 1e12,
            "note": "backward timed with its one stream synchronization (the column count) inside"}

@@ -238,6 +238,11 @@ int tdc_syev_tridiag_batched(int32_t batch, const int64_t* n_host, const int64_t
  * skipped (the call synchronizes the stream once to count them).
  *   lambda, Q (ld = ldq): the forward output;  g_lambda, g_Q (ld = ldg): may be NULL;
  *   g_d (n), g_e (n - 1): outputs.  Workspace: tdc_backward_workspace_bytes(n, opts).
+ * The two products with Q (Q^T Qbar_S and Q M_S) run in FP64, or on the split-precision
+ * tensor-core path when opts->path is TDC_PATH_DENSE_OZAKI (7 bf16 slices whatever
+ * opts->ozaki_slices says, since the eigenvector term multiplies the products' error by
+ * up to 1 / min |lambda_c - lambda_i|).  dev_status (may be NULL) gets bit 8 if a
+ * tensor-core wait timed out.
  */
 size_t tdc_backward_workspace_bytes(int64_t n, const tdc_opts* opts);
 int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, int64_t ldq,

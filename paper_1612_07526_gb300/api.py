@@ -353,26 +353,29 @@ class HostPipeline:
         return 8 * (self.n + self.n * self.n)
 
 
-def syev_backward(lam: torch.Tensor, q: torch.Tensor, g_lam=None, g_q=None, stream=None):
+def syev_backward(lam: torch.Tensor, q: torch.Tensor, g_lam=None, g_q=None, stream=None, opts=None):
     """(g_d, g_e) of a loss with gradients (g_lam, g_q) at the output (lam, q) of
-    syev_tridiag, through tdc_syev_tridiag_backward (band-only adjoint)."""
+    syev_tridiag, through tdc_syev_tridiag_backward (band-only adjoint).  opts with
+    path 1 runs its two products with Q on the split-precision tensor-core path."""
     lib = _lib.load()
     n = int(lam.shape[0])
     if g_q is not None and g_q.stride() != (1, n):
         g_q = g_q.t().contiguous().t()                 # column-major layout expected by the ABI
     gd = torch.empty(n, dtype=torch.float64, device=lam.device)
     ge = torch.empty(max(n - 1, 0), dtype=torch.float64, device=lam.device)
-    nb = lib.tdc_backward_workspace_bytes(n, None)
+    o = _opts(opts) if opts is not None else None
+    op = ctypes.byref(o) if o is not None else None
+    nb = lib.tdc_backward_workspace_bytes(n, op)
     ws = workspace(nb, lam.device, key="backward")
     rc = lib.tdc_syev_tridiag_backward(n, _vp(lam), _vp(q), n, _vp(g_lam), _vp(g_q), n, _vp(gd),
-                                       _vp(ge if n > 1 else None), None, _vp(ws), ws.numel(), None,
+                                       _vp(ge if n > 1 else None), op, _vp(ws), ws.numel(), None,
                                        _stream(stream))
     _check_rc(rc, "tdc_syev_tridiag_backward")
     return gd, ge
 
 
 def syev_backward_batched(sizes, lam_cat: torch.Tensor, q_cat: torch.Tensor, g_lam_cat=None, g_q_cat=None,
-                          max_cols: int = -1, stream=None):
+                          max_cols: int = -1, stream=None, opts=None):
     """(g_d_cat, g_e_cat) for a batch in the batched forward's dense packing
     (tdc_syev_tridiag_backward_batched): lam_cat / g_lam_cat hold sum(n) values,
     q_cat / g_q_cat the n_p x n_p column-major blocks back to back; g_e_cat holds
@@ -385,12 +388,14 @@ def syev_backward_batched(sizes, lam_cat: torch.Tensor, q_cat: torch.Tensor, g_l
     gd = torch.empty(tot, dtype=torch.float64, device=dev)
     ge = torch.zeros(tot, dtype=torch.float64, device=dev)
     sp = sizes.ctypes.data_as(ctypes.c_void_p)
-    nb = lib.tdc_backward_batched_workspace_bytes(b, sp, int(max_cols), None)
+    o = _opts(opts) if opts is not None else None
+    op = ctypes.byref(o) if o is not None else None
+    nb = lib.tdc_backward_batched_workspace_bytes(b, sp, int(max_cols), op)
     if nb == 0:
         raise ValueError("invalid sizes")
     ws = workspace(nb, dev, key="backward_batched")
     rc = lib.tdc_syev_tridiag_backward_batched(b, sp, _vp(lam_cat), _vp(q_cat), _vp(g_lam_cat), _vp(g_q_cat),
-                                               _vp(gd), _vp(ge), None, _vp(ws), ws.numel(), None, _stream(stream))
+                                               _vp(gd), _vp(ge), op, _vp(ws), ws.numel(), None, _stream(stream))
     _check_rc(rc, "tdc_syev_tridiag_backward_batched")
     return gd, ge
 
@@ -403,12 +408,13 @@ class TridiagEigh(torch.autograd.Function):
     def forward(ctx, d, e, opts=None):
         lam, q = syev_tridiag(d.detach().contiguous(), e.detach().contiguous(), opts=opts)
         ctx.save_for_backward(lam, q)
+        ctx.opts = opts
         return lam, q
 
     @staticmethod
     def backward(ctx, g_lam, g_q):
         lam, q = ctx.saved_tensors
-        gd, ge = syev_backward(lam, q, g_lam, g_q)
+        gd, ge = syev_backward(lam, q, g_lam, g_q, opts=ctx.opts)
         return gd, ge, None
 
 

@@ -19,6 +19,7 @@
 #include "../../include/tdc.h"
 #include "tdc_hss.cuh"
 #include "tdc_internal.cuh"
+#include "tdc_ozaki.cuh"
 
 namespace tdc {
 namespace {
@@ -207,6 +208,7 @@ struct BwLayout {
   double* G;             // sum n s each: G (then M), P, W
   double* P;
   double* W;
+  int* status_scratch;   // the split products' wait status when the caller passes none
   size_t fixed;          // bytes before G
 };
 
@@ -223,6 +225,7 @@ BwLayout bw_layout(unsigned char* b, int nb, int64_t vtot) {
   L.flag = reinterpret_cast<int*>(take(sizeof(int) * vtot));
   L.cols = reinterpret_cast<int*>(take(sizeof(int) * vtot));
   L.tab = take(kBwTab);
+  L.status_scratch = reinterpret_cast<int*>(take(16));
   L.fixed = off;
   return L;
 }
@@ -232,17 +235,31 @@ BwLayout bw_layout(unsigned char* b, int nb, int64_t vtot) {
 
 using namespace tdc;
 
+namespace {
+// The backward's two products run on the split-precision tensor-core path when the
+// options select the split product (path TDC_PATH_DENSE_OZAKI), in FP64 otherwise.  They
+// use 7 slices whatever opts->ozaki_slices says: the eigenvector term multiplies the
+// error of Q^T Qbar by 1/(lambda_c - lambda_i), up to about 1e5 on the n = 4096
+// configuration, and 6 slices (about 2e-14 per product) left 2e-9 relative in the
+// gradient against 2e-10 with 7.
+bool bw_split(const tdc_opts* opts) { return opts && opts->path == TDC_PATH_DENSE_OZAKI; }
+int bw_slices(const tdc_opts*) { return 7; }
+}  // namespace
+
 extern "C" size_t tdc_backward_workspace_bytes(int64_t n, const tdc_opts* opts) {
-  (void)opts;
   if (n < 1) return 0;
-  return al(n * 4) + al(n * 4) + al(16) + 3 * al((size_t)n * n * 8) + al(1 << 20);
+  size_t b = al(n * 4) + al(n * 4) + al(16) + 3 * al((size_t)n * n * 8) + al(1 << 20);
+  if (bw_split(opts) && n <= INT32_MAX) {
+    const std::vector<SgProblem> pr{SgProblem{(int)n, (int)n, (int)n, nullptr, 0, 0, nullptr, 0, nullptr, 0}};
+    b += al(split_gemm_bytes(pr, bw_slices(opts)));
+  }
+  return b;
 }
 
 extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const double* Q, int64_t ldq,
                                          const double* g_lambda, const double* g_Q, int64_t ldg, double* g_d,
                                          double* g_e, const tdc_opts* opts, void* ws, size_t ws_bytes,
                                          int* dev_status, void* stream) {
-  (void)dev_status;
   if (n < 1) return -1;
   if (!lambda) return -2;
   if (!Q) return -3;
@@ -278,19 +295,33 @@ extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const 
   if (s > 0) {
     const int64_t ne = n * s;
     k_bw_gather<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(g_Q, ldg, n, cols, s, G);
-    std::vector<HGemm> g(1);
-    std::memset(g.data(), 0, sizeof(HGemm));
-    g[0].M = (int)n; g[0].N = s; g[0].K = (int)n;          // P = Q^T G
-    g[0].a.mode = HOP_DENSE_T; g[0].a.p = Q; g[0].a.ld = ldq;
-    g[0].b.mode = HOP_DENSE; g[0].b.p = G; g[0].b.ld = n;
-    g[0].C = P; g[0].ldc = n; g[0].alpha = 1.0;
-    size_t toff = 0;
-    launch_dense_gemms(g, tab, toff, st);
-    k_bw_m<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P, lambda, cols, n, s, G);   // M_S into G
-    g[0].a.mode = HOP_DENSE; g[0].a.p = Q; g[0].a.ld = ldq;                            // W = Q M_S
-    g[0].b.p = G;
-    g[0].C = W;
-    launch_dense_gemms(g, tab, toff, st);
+    if (bw_split(opts)) {
+      // the split-precision arena follows the FP64 path's buffers
+      unsigned char* arena = b + off;
+      const size_t abytes = ws_bytes > off ? ws_bytes - off : 0;
+      std::vector<SgProblem> pr{SgProblem{(int)n, s, (int)n, Q, ldq, 1, G, n, P, n}};   // P = Q^T G
+      int* err = dev_status ? dev_status : ns_dev + 1;      // a timed-out tensor-core wait sets bit 8 here
+      int rc = split_gemm(pr, bw_slices(opts), arena, abytes, err, st);
+      if (rc) return rc;
+      k_bw_m<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P, lambda, cols, n, s, G);   // M_S into G
+      pr[0] = SgProblem{(int)n, s, (int)n, Q, ldq, 0, G, n, W, n};                      // W = Q M_S
+      rc = split_gemm(pr, bw_slices(opts), arena, abytes, err, st);
+      if (rc) return rc;
+    } else {
+      std::vector<HGemm> g(1);
+      std::memset(g.data(), 0, sizeof(HGemm));
+      g[0].M = (int)n; g[0].N = s; g[0].K = (int)n;          // P = Q^T G
+      g[0].a.mode = HOP_DENSE_T; g[0].a.p = Q; g[0].a.ld = ldq;
+      g[0].b.mode = HOP_DENSE; g[0].b.p = G; g[0].b.ld = n;
+      g[0].C = P; g[0].ldc = n; g[0].alpha = 1.0;
+      size_t toff = 0;
+      launch_dense_gemms(g, tab, toff, st);
+      k_bw_m<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P, lambda, cols, n, s, G);   // M_S into G
+      g[0].a.mode = HOP_DENSE; g[0].a.p = Q; g[0].a.ld = ldq;                            // W = Q M_S
+      g[0].b.p = G;
+      g[0].C = W;
+      launch_dense_gemms(g, tab, toff, st);
+    }
   }
   k_bw_band<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Q, ldq, n, lambda, g_lambda, W, cols, s, g_d, g_e);
   return cudaGetLastError() == cudaSuccess ? 0 : 4;
@@ -298,7 +329,6 @@ extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const 
 
 extern "C" size_t tdc_backward_batched_workspace_bytes(int32_t batch, const int64_t* n_host, int64_t max_cols,
                                                        const tdc_opts* opts) {
-  (void)opts;
   if (batch < 1 || !n_host) return 0;
   int64_t vtot = 0, ns = 0;
   for (int p = 0; p < batch; ++p) {
@@ -308,7 +338,18 @@ extern "C" size_t tdc_backward_batched_workspace_bytes(int32_t batch, const int6
     ns += n_host[p] * std::max<int64_t>(s, 1);
   }
   const BwLayout L = bw_layout(nullptr, batch, vtot);
-  return L.fixed + 3 * al((size_t)ns * 8) + 256;
+  size_t bytes = L.fixed + 3 * al((size_t)ns * 8) + 256;
+  if (bw_split(opts)) {
+    std::vector<SgProblem> pr;
+    for (int p = 0; p < batch; ++p) {
+      const int64_t s = max_cols < 0 ? n_host[p] : std::min<int64_t>(max_cols, n_host[p]);
+      if (n_host[p] > INT32_MAX) return 0;
+      pr.push_back(SgProblem{(int)n_host[p], (int)std::max<int64_t>(s, 1), (int)n_host[p], nullptr, 0, 0, nullptr,
+                             0, nullptr, 0});
+    }
+    bytes += al(split_gemm_bytes(pr, bw_slices(opts)));
+  }
+  return bytes;
 }
 
 extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n_host, const double* lambda_cat,
@@ -316,8 +357,6 @@ extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n
                                                  const double* g_Q_cat, double* g_d_cat, double* g_e_cat,
                                                  const tdc_opts* opts, void* ws, size_t ws_bytes, int* dev_status,
                                                  void* stream) {
-  (void)opts;
-  (void)dev_status;
   if (batch < 1) return -1;
   if (!n_host) return -2;
   if (!lambda_cat) return -3;
@@ -372,6 +411,26 @@ extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n
   if (ns > 0) {
     const unsigned gb = grid_cap((ns + 255) / 256, 8);
     k_bwb_gather<<<gb, 256, 0, st>>>(L.prob, batch, cum_ns, ns, g_Q_cat, L.cols, L.G);
+    if (bw_split(opts)) {
+      std::vector<SgProblem> pa, pw;
+      for (int p = 0; p < batch; ++p) {
+        if (pr[p].s == 0) continue;
+        const int n = (int)pr[p].n;
+        pa.push_back(SgProblem{n, pr[p].s, n, Q_cat + pr[p].q, n, 1, L.G + pr[p].g, n, L.P + pr[p].g, n});   // Q^T G
+        pw.push_back(SgProblem{n, pr[p].s, n, Q_cat + pr[p].q, n, 0, L.G + pr[p].g, n, L.W + pr[p].g, n});   // Q M
+      }
+      unsigned char* arena = b + off;
+      const size_t abytes = ws_bytes > off ? ws_bytes - off : 0;
+      int* err = dev_status ? dev_status : L.status_scratch;
+      int rc = split_gemm(pa, bw_slices(opts), arena, abytes, err, st);
+      if (rc) return rc;
+      k_bwb_m<<<gb, 256, 0, st>>>(L.prob, batch, cum_ns, ns, L.P, lambda_cat, L.cols, L.G);   // M into G
+      rc = split_gemm(pw, bw_slices(opts), arena, abytes, err, st);
+      if (rc) return rc;
+      k_bwb_band<<<(unsigned)((vtot + 255) / 256), 256, 0, st>>>(L.prob, batch, cum_n, vtot, Q_cat, g_lambda_cat,
+                                                                 L.W, L.cols, g_d_cat, g_e_cat);
+      return cudaGetLastError() == cudaSuccess ? 0 : 4;
+    }
     std::vector<HGemm> g;
     for (int p = 0; p < batch; ++p) {           // P = Q^T G
       if (pr[p].s == 0) continue;

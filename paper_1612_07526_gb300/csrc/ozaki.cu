@@ -186,8 +186,6 @@ __device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-// 2^e for e in the normal range, built from its bit pattern (exact).
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
 // The epilogue's conversions and power-of-two scalings on the integer pipes, from the
 // IEEE-754 binary64/binary32 formats (GB300's FP64 pipe issues 2 lanes per clock per SM,
@@ -833,6 +831,422 @@ bool encode4d(CUtensorMap* map, void* base, int64_t ldk, int64_t rows, int slice
 
 int64_t job_ldk(const MergeJob& J) { return rup((int64_t)J.n1 + J.n2 + 3 * kOzPad, kOzPad); }
 
+// ------------------------------------------------------------------------ dense split GEMM
+// C_j = A_j B_j for a batch of dense column-major problems (A_j: M x K, or given as its
+// transpose; B_j: K x N), with the merge product's splitting, tensor-core schedule and
+// epilogue: A's rows and B's columns are scaled by powers of two (2^aexp[r], 2^bexp[c])
+// and split into S bf16 digit slices in the k-blocked layout, and a persistent tcgen05
+// kernel forms the 128 x 64 tiles.  Used for the backward's products.
+struct SgJob {                       // CUtensorMap members force 64-byte alignment
+  CUtensorMap mapA, mapB;            // slices: [slice][k / 32][row or column][32]
+  const double* a;                   // A[r, k] = a[r + k lda] (atrans 0) or a[k + r lda] (atrans 1)
+  const double* b;                   // B[k, c] = b[k + c ldb]
+  double* C;                         // C[r, c] = C[r + c ldc]
+  uint16_t *as, *bs;
+  int32_t *aexp, *bexp;              // INT32_MIN: a zero row / column
+  int64_t lda, ldb, ldc;
+  int32_t M, N, K, Kp;               // Kp: K rounded up to 64
+  int32_t atrans, pad_;
+};
+
+// rows of A, 32 per block: the row's power of two, then its digits, 64 k at a time
+// through shared memory; lanes run along whichever index is contiguous in memory
+template <int S>
+__global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jobs, int njobs,
+                                                    const int64_t* __restrict__ cum) {
+  __shared__ double tile[64][33];
+  __shared__ unsigned long long s_max[8][32];
+  __shared__ int s_exp[32];
+  const int jb = find_job(cum, njobs, blockIdx.x);
+  const SgJob& J = jobs[jb];
+  const int r0 = (int)(blockIdx.x - cum[jb]) * 32;
+  const int tid = threadIdx.x;
+  const int M = J.M, K = J.K;
+  auto at = [&](int r, int k) -> double {          // A[r0 + r, k], zero outside
+    if (r0 + r >= M || k >= K) return 0.0;
+    return J.atrans ? J.a[(int64_t)k + (int64_t)(r0 + r) * J.lda] : J.a[(int64_t)(r0 + r) + (int64_t)k * J.lda];
+  };
+  // pass 1: row maxima on the magnitude bits
+  unsigned long long mx = 0ull;
+  if (!J.atrans) {
+    const int r = tid & 31, kq = tid >> 5;
+    for (int k = kq; k < K; k += 8) {
+      const unsigned long long v = (unsigned long long)__double_as_longlong(at(r, k)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = v > mx ? v : mx;
+    }
+    s_max[kq][r] = mx;
+  } else {                                          // a warp per group of four rows, lanes along k
+    const int lane = tid & 31, wq = tid >> 5;
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = wq * 4 + rr;
+      unsigned long long m = 0ull;
+      for (int k = lane; k < K; k += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(at(r, k)) & 0x7FFFFFFFFFFFFFFFull;
+        m = v > m ? v : m;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+      }
+      if (lane == 0) s_max[0][r] = m;
+    }
+    if (tid < 32)
+      for (int q = 1; q < 8; ++q) s_max[q][tid] = 0ull;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    unsigned long long mb = s_max[0][tid];
+    for (int q = 1; q < 8; ++q) mb = s_max[q][tid] > mb ? s_max[q][tid] : mb;
+    const double m = __longlong_as_double((long long)mb);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);                      // m < 2^e
+    s_exp[tid] = e;
+    if (r0 + tid < M) J.aexp[r0 + tid] = m > 0.0 ? e : INT32_MIN;
+  }
+  __syncthreads();
+  // pass 2: digits
+  const int wr = tid >> 3, wk = (tid & 7) * 8;
+  const int shift = 8 * S - 1 - s_exp[wr];
+  for (int k0 = 0; k0 < J.Kp; k0 += 64) {
+    if (!J.atrans) {
+      const int r = tid & 31, kq = tid >> 5;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) tile[kq * 8 + kk][r] = at(r, k0 + kq * 8 + kk);
+    } else {
+      const int k = tid & 63, rq = tid >> 6;
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) tile[k][rq * 8 + rr] = at(rq * 8 + rr, k0 + k);
+    }
+    __syncthreads();
+    if (r0 + wr < M) {
+      uint16_t dg[8][S];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint16_t t[S];
+        digits_bf16<S>(round_scaled(tile[wk + j][wr], shift), t);
+#pragma unroll
+        for (int p = 0; p < S; ++p) dg[j][p] = t[p];
+      }
+      const int k = k0 + wk;
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
+        uint4 v;
+        v.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+        v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+        v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+        v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+        *reinterpret_cast<uint4*>(J.as + (((int64_t)p * (J.Kp / kOzBK) + k / kOzBK) * M + r0 + wr) * kOzBK +
+                                  (k % kOzBK)) = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// columns of B, a warp per column (8 per block): the column's power of two, then its
+// digits, each lane 8 consecutive k
+template <int S>
+__global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jobs, int njobs,
+                                                    const int64_t* __restrict__ cum) {
+  const int jb = find_job(cum, njobs, blockIdx.x);
+  const SgJob& J = jobs[jb];
+  const int lane = threadIdx.x & 31;
+  const int c = (int)(blockIdx.x - cum[jb]) * 8 + (int)(threadIdx.x >> 5);
+  if (c >= J.N) return;                             // uniform over the warp
+  const double* col = J.b + (int64_t)c * J.ldb;
+  unsigned long long m = 0ull;
+  for (int k = lane; k < J.K; k += 32) {
+    const unsigned long long v = (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull;
+    m = v > m ? v : m;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  const double mv = __longlong_as_double((long long)m);
+  int e = 0;
+  if (mv > 0.0) frexp(mv, &e);
+  if (lane == 0) J.bexp[c] = mv > 0.0 ? e : INT32_MIN;
+  const int shift = 8 * S - 1 - e;
+  for (int k0 = lane * 8; k0 < J.Kp; k0 += 256) {
+    uint16_t dg[8][S];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint16_t t[S];
+      digits_bf16<S>(round_scaled(k0 + j < J.K ? col[k0 + j] : 0.0, shift), t);
+#pragma unroll
+      for (int p = 0; p < S; ++p) dg[j][p] = t[p];
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      uint4 v;
+      v.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+      v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+      v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+      v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+      *reinterpret_cast<uint4*>(J.bs + (((int64_t)p * (J.Kp / kOzBK) + k0 / kOzBK) * J.N + c) * kOzBK +
+                                (k0 % kOzBK)) = v;
+    }
+  }
+}
+
+// The persistent GEMM over the batch's 128 x 64 tiles (cum: tiles of the jobs before
+// j).  Same roles, barriers, MMA schedule and epilogue combination as k_oz_gemm; the
+// k range is the whole padded K of the job.
+struct SgTile {
+  int jb, row0, ct, nst, nchunks;
+};
+__device__ __forceinline__ SgTile sg_tile(const SgJob* __restrict__ jobs, const int64_t* __restrict__ cum,
+                                          int njobs, int64_t t) {
+  SgTile v;
+  v.jb = find_job(cum, njobs, t);
+  const int64_t local = t - cum[v.jb];
+  const int nct = (jobs[v.jb].N + kOzBN - 1) / kOzBN;
+  v.ct = (int)(local % nct);
+  v.row0 = (int)(local / nct) * kOzBM;
+  v.nst = jobs[v.jb].Kp / kOzBK;
+  v.nchunks = (v.nst + kOzChunk / kOzBK - 1) / (kOzChunk / kOzBK);
+  return v;
+}
+
+template <int S>
+__global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict__ jobs, int njobs,
+                                                         const int64_t* __restrict__ cum, int* err0) {
+  using C = OzCfg<S>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::ST * C::STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::ST + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int64_t total = cum[njobs];
+  if ((int64_t)blockIdx.x >= total) return;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (C::ST + s); };
+  const uint32_t accfull = bar0 + 8u * (2 * C::ST);
+  const uint32_t accempty = bar0 + 8u * (2 * C::ST + 1);
+  const uint32_t done = bar0 + 8u * (2 * C::ST + 2);
+  const uint32_t tfree = bar0 + 8u * (2 * C::ST + 3);
+  int* err = err0;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::ST; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, kEpiWarps);
+    mbar_init(done, 1);
+    mbar_init(tfree, kEpiWarps);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp >= 2) {
+    const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(((warp - 2) >> 2) * 32);
+#pragma unroll
+    for (int L = 0; L < C::NL; ++L) tmem_st32_zero(tq + (uint32_t)(L * kOzBN));
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      uint32_t g = 0, issued_total = 0;
+      for (int64_t t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        const SgTile T = sg_tile(jobs, cum, njobs, t);
+        const CUtensorMap* mA = &jobs[T.jb].mapA;
+        const CUtensorMap* mB = &jobs[T.jb].mapB;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(mA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(mB) : "memory");
+        bool ok = true;
+        for (int it = 0; it < T.nst; ++it, ++g) {
+          const int s = (int)(g % C::ST);
+          const uint32_t ph = (g / C::ST) & 1u;
+          if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          mbar_expect_tx(full(s), C::STAGE);
+          tma_load_4d(sa, mA, full(s), 0, T.row0, it, 0);
+          tma_load_4d(sa + C::A_BYTES, mB, full(s), 0, T.ct * kOzBN, it, 0);
+          issued_total = g + 1;
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag) {
+        const long long t0 = global_ns();
+        for (uint32_t q = (issued_total > (uint32_t)C::ST ? issued_total - C::ST : 0u); q < issued_total; ++q) {
+          const uint32_t ph = (q / C::ST) & 1u;
+          while (!mbar_try(full((int)(q % C::ST)), ph) && global_ns() - t0 < kWaitNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const int per_chunk = kOzChunk / kOzBK;
+      uint32_t g = 0, cg = 0, ti = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const SgTile T = sg_tile(jobs, cum, njobs, t);
+        if (T.nst == 0) continue;
+        if (ti > 0) {
+          if (!mbar_wait(tfree, (ti - 1) & 1u, abort_flag, err)) { ok = false; break; }
+          tc_fence_after();
+        }
+        for (int it = 0; it < T.nst; ++it, ++g) {
+          const int s = (int)(g % C::ST);
+          const uint32_t ph = (g / C::ST) & 1u;
+          if (!mbar_wait(full(s), ph, abort_flag, err)) { ok = false; break; }
+          tc_fence_after();
+          const int chunk = it / per_chunk;
+          const bool first = (it % per_chunk) == 0;
+          const bool last = (it % per_chunk) == per_chunk - 1 || it == T.nst - 1;
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < kOzBK / 16; ++kk) {
+#pragma unroll
+            for (int p = 1; p <= S; ++p) {
+#pragma unroll
+              for (int qa = 1; qa <= 5; qa += 4) {
+                if (qa <= C::qmax(p) && p + qa >= 6) {
+                  const int nq = C::qmax(p) - qa + 1 < 4 ? C::qmax(p) - qa + 1 : 4;
+                  tc_mma(tmem + (uint32_t)((p + qa - 2) * kOzBN),
+                         sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                         sdesc(sb + (qa - 1) * (kOzBN * kOzBK * 2) + kk * 32), idesc_n(nq), 1u);
+                }
+              }
+            }
+            if (first && kk == 0 && chunk > 0) {
+              if (!mbar_wait(accempty, (cg - 1) & 1u, abort_flag, err)) { ok = false; break; }
+              tc_fence_after();
+            }
+#pragma unroll
+            for (int p = 1; p <= 4; ++p) {
+              const int nq = C::qmax(p) < 4 ? C::qmax(p) : 4;
+              const uint32_t acc = (p == 1 && first && kk == 0) ? 0u : 1u;
+              tc_mma(tmem + (uint32_t)((p - 1) * kOzBN), sdesc(sa + (p - 1) * (kOzBM * kOzBK * 2) + kk * 32),
+                     sdesc(sb + kk * 32), idesc_n(nq), acc);
+            }
+          }
+          if (!ok) break;
+          tc_commit(empty(s));
+          if (last) {
+            tc_commit(accfull);
+            ++cg;
+          }
+        }
+        if (!ok) break;
+        tc_commit(done);
+        ++ti;
+      }
+      if (*abort_flag) {
+        tc_commit(done);
+        const long long t0 = global_ns();
+        if (ti > 0)
+          while (!mbar_try(done, (ti - 1) & 1u) && global_ns() - t0 < kWaitNs) {
+          }
+        while (!mbar_try(done, ti & 1u) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue (as k_oz_gemm's)
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 32);
+    uint32_t cg = 0, ti = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+      const SgTile T = sg_tile(jobs, cum, njobs, t);
+      const SgJob& J = jobs[T.jb];
+      long long acc[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < T.nchunks; ++c) {
+        const bool got = __all_sync(0xffffffffu, mbar_wait(accfull, cg & 1u, abort_flag, err));
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int L = 2; L <= 5; ++L) {
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            acc[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (5 - L));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty);
+        ++cg;
+      }
+      float tsum[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tsum[j] = 0.0f;
+      if (ok && T.nst > 0) {
+        ok = __all_sync(0xffffffffu, mbar_wait(done, ti & 1u, abort_flag, err));
+        if (ok) {
+          tc_fence_after();
+#pragma unroll
+          for (int L = S + 2; L >= 6; --L) {
+            uint32_t v[32];
+            tmem_ld32(trow + (uint32_t)((L - 2) * kOzBN), v);
+            tmem_wait_ld();
+            const float wL = __int_as_float((127 - 8 * (L - 6)) << 23);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tsum[j] = fmaf(__uint_as_float(v[j]), wL, tsum[j]);
+          }
+#pragma unroll
+          for (int L = 6; L <= S + 2; ++L) tmem_st32_zero(trow + (uint32_t)((L - 2) * kOzBN));
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tfree);
+          ++ti;
+        }
+      }
+      if (!ok) break;
+      const int grow = T.row0 + row;
+      if (grow < J.M) {
+        const int ea = J.aexp[grow];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = T.ct * kOzBN + half * 32 + j;
+          if (col < J.N) {
+            const int eb = J.bexp[col];
+            J.C[(int64_t)grow + (int64_t)col * J.ldc] =
+                (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
 }  // namespace
 
 size_t oz_job_bytes(const MergeJob& J, int slices) {
@@ -883,6 +1297,107 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
     case 5: launch_s<5>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
     case 7: launch_s<7>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
     default: launch_s<6>(part, jobs, ozj, njobs, cum_sa, nb_sa, cum_sb, nb_sb, cum_t, ntiles, qb, w, st); break;
+  }
+}
+
+size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
+  const int S = slices < 5 ? 5 : (slices > 7 ? 7 : slices);
+  size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 3 * rup(((int64_t)pr.size() + 1) * 8, 256);
+  for (const SgProblem& p : pr) {
+    const int64_t Kp = rup(p.K, 64);
+    b += rup((int64_t)S * p.M * Kp * 2, 256) + rup((int64_t)S * p.N * Kp * 2, 256) + rup((int64_t)p.M * 4, 256) +
+         rup((int64_t)p.N * 4, 256);
+  }
+  return b + 256;
+}
+
+namespace {
+template <int S>
+int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_bytes, int* err, cudaStream_t st) {
+  using C = OzCfg<S>;
+  static std::mutex mu;
+  static bool attr[64] = {};
+  static int sms[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nsm = 148;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+      cudaFuncSetAttribute(k_sg_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      int n = 0;
+      if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+      if (dev >= 0 && dev < 64) {
+        attr[dev] = true;
+        sms[dev] = n;
+      }
+      nsm = n;
+    } else {
+      nsm = sms[dev];
+    }
+  }
+  const size_t nj = pr.size();
+  size_t off = (256 - (reinterpret_cast<uintptr_t>(ws) & 255)) & 255;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = ws + off;
+    off = (size_t)rup((int64_t)(off + bytes), 256);
+    return p;
+  };
+  SgJob* djobs = reinterpret_cast<SgJob*>(take(nj * sizeof(SgJob)));
+  int64_t* dca = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
+  int64_t* dcb = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
+  int64_t* dct = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
+  std::vector<SgJob> jobs(nj);
+  std::vector<int64_t> ca(nj + 1, 0), cb(nj + 1, 0), ct(nj + 1, 0);
+  for (size_t j = 0; j < nj; ++j) {
+    const SgProblem& p = pr[j];
+    SgJob& J = jobs[j];
+    std::memset(&J, 0, sizeof(J));
+    J.M = p.M;
+    J.N = p.N;
+    J.K = p.K;
+    J.Kp = (int32_t)rup(p.K, 64);
+    J.a = p.a;
+    J.lda = p.lda;
+    J.atrans = p.atrans;
+    J.b = p.b;
+    J.ldb = p.ldb;
+    J.C = p.C;
+    J.ldc = p.ldc;
+    J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
+    J.bs = reinterpret_cast<uint16_t*>(take((size_t)S * p.N * J.Kp * 2));
+    J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));
+    J.bexp = reinterpret_cast<int32_t*>(take((size_t)p.N * 4));
+    if (!encode4d(&J.mapA, J.as, J.Kp, p.M, S, kOzBM) || !encode4d(&J.mapB, J.bs, J.Kp, p.N, S, kOzBN)) return 4;
+    ca[j + 1] = ca[j] + (p.M + 31) / 32;
+    cb[j + 1] = cb[j] + (p.N + 7) / 8;
+    ct[j + 1] = ct[j] + (int64_t)((p.M + kOzBM - 1) / kOzBM) * ((p.N + kOzBN - 1) / kOzBN);
+  }
+  if (off > ws_bytes) return 3;
+  cudaMemcpyAsync(djobs, jobs.data(), nj * sizeof(SgJob), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dca, ca.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dcb, cb.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dct, ct.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
+  if (ca[nj]) k_sg_slice_a<S><<<(unsigned)ca[nj], 256, 0, st>>>(djobs, (int)nj, dca);
+  if (cb[nj]) k_sg_slice_b<S><<<(unsigned)cb[nj], 256, 0, st>>>(djobs, (int)nj, dcb);
+  if (ct[nj]) {
+    const unsigned grid = (unsigned)(ct[nj] < nsm ? ct[nj] : nsm);
+    k_sg_gemm<S><<<grid, kThreads, C::SMEM, st>>>(djobs, (int)nj, dct, err);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+}  // namespace
+
+int split_gemm(const std::vector<SgProblem>& pr, int slices, unsigned char* ws, size_t ws_bytes, int* dev_err,
+               cudaStream_t st) {
+  if (pr.empty()) return 0;
+  for (const SgProblem& p : pr)
+    if (p.M < 1 || p.N < 1 || p.K < 1 || !p.a || !p.b || !p.C) return -1;
+  if (ws_bytes < split_gemm_bytes(pr, slices)) return 3;
+  switch (slices < 5 ? 5 : (slices > 7 ? 7 : slices)) {
+    case 5: return split_gemm_s<5>(pr, ws, ws_bytes, dev_err, st);
+    case 7: return split_gemm_s<7>(pr, ws, ws_bytes, dev_err, st);
+    default: return split_gemm_s<6>(pr, ws, ws_bytes, dev_err, st);
   }
 }
 

@@ -56,6 +56,27 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
                         int64_t ntiles, int slices, QBufs qb, DevWs w, cudaStream_t st);
 // bf16 slice products per FP64-equivalent product: pairs (p, q) with p + q <= S + 2.
 int oz_slice_pairs(int slices);
+
+// Dense products C = A B on the same split-precision tensor-core path (the backward's
+// Q^T G and Q M): A is M x K, column-major with leading dimension lda, or given as its
+// transpose (atrans: A[r, k] = a[k + r lda]); B is K x N column-major; C is M x N
+// column-major and is overwritten.  One call runs a batch: slicing of every A and B,
+// then one persistent GEMM over all their tiles.  The workspace holds the slices
+// (about 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives
+// its size.  Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
+struct SgProblem {
+  int M, N, K;
+  const double* a;
+  int64_t lda;
+  int atrans;
+  const double* b;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+};
+size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices);
+int split_gemm(const std::vector<SgProblem>& pr, int slices, unsigned char* ws, size_t ws_bytes, int* dev_err,
+               cudaStream_t st);
 // Units per job for the three launches (host).
 int64_t oz_blocks_slice_a(const MergeJob& J);
 int64_t oz_blocks_slice_b(const MergeJob& J);

@@ -113,6 +113,11 @@ def test_backward_config_size_finite_differences(api):
     scale = max(np.abs(rd).max(), np.abs(re).max())
     assert np.max(np.abs(grad[:n] - rd)) <= 1e-9 * scale
     assert np.max(np.abs(grad[n:] - re)) <= 1e-9 * scale
+    # the same gradient with the products on the split-precision path (7 slices)
+    gd_s, ge_s = api.syev_backward(lam.detach(), q.detach(), torch.tensor(gl, device="cuda"),
+                                   torch.tensor(gq, device="cuda"), opts={"path": 1})
+    assert np.max(np.abs(gd_s.cpu().numpy() - rd)) <= 1e-9 * scale
+    assert np.max(np.abs(ge_s.cpu().numpy() - re)) <= 1e-9 * scale
 
 
 def _batched_case(api, sizes, m, seed):
@@ -185,3 +190,50 @@ def test_backward_batched_lambda_only_and_workspace_limit(api):
                                                api._vp(gq_cat), api._vp(out), api._vp(out.clone()), None,
                                                api._vp(wsb), nb, None, api._stream(None))
     assert rc == 3
+
+
+@pytest.mark.parametrize("n,m", [(200, 8), (1024, 64), (1000, 37)])
+def test_backward_split_products(api, n, m):
+    """The backward with its two products on the split-precision tensor-core path
+    (opts path 1, 7 slices): within 1e-10 of the FP64 backward (the products' error of
+    about 2^-56 relative to their row and column scales, times the eigenvector term's
+    1/gap amplification, below 1e4 at these sizes) and within the dense reference's
+    bound; ragged sizes exercise partial tiles in rows, columns and k."""
+    d, e = W.normal_tridiag(n, 140 + n)
+    w = W.gaussian(n, 141)
+    G = W.gaussian((n, m), 142)
+    lam, q = api.syev_tridiag(torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda"))
+    lam_n, q_n = lam.cpu().numpy(), q.cpu().numpy()
+    gl, gq = backward.config_loss_grads(lam_n, q_n, w, G)
+    glt, gqt = torch.tensor(gl, device="cuda"), torch.tensor(gq, device="cuda")
+    gd0, ge0 = api.syev_backward(lam, q, glt, gqt)
+    gd1, ge1 = api.syev_backward(lam, q, glt, gqt, opts={"path": 1})
+    rd, re = backward.band_gradient(lam_n, q_n, gl, gq)
+    scale = max(np.abs(rd).max(), np.abs(re).max())
+    assert torch.max(torch.abs(gd1 - gd0)).item() <= 1e-10 * scale
+    assert torch.max(torch.abs(ge1 - ge0)).item() <= 1e-10 * scale
+    assert np.max(np.abs(gd1.cpu().numpy() - rd)) <= 1e-9 * scale
+    assert np.max(np.abs(ge1.cpu().numpy() - re)) <= 1e-9 * scale
+
+
+def test_backward_batched_split_products(api):
+    """The batched backward on the split path: each problem equals the single-problem
+    split backward bit for bit (its slices and tiles do not depend on the batch) and
+    stays within 1e-10 of the FP64 batched backward."""
+    sizes, m = [1, 2, 33, 200, 64, 300, 513], 16
+    ds, es, ws, Gs, lam, q, sz, qoff, gl_cat, gq_cat = _batched_case(api, sizes, m, 180)
+    gd0, ge0 = api.syev_backward_batched(sz, lam, q, gl_cat, gq_cat, max_cols=m)
+    gd, ge = api.syev_backward_batched(sz, lam, q, gl_cat, gq_cat, max_cols=m, opts={"path": 1})
+    scale = max(torch.max(torch.abs(gd0)).item(), torch.max(torch.abs(ge0)).item())
+    assert torch.max(torch.abs(gd - gd0)).item() <= 1e-10 * scale
+    assert torch.max(torch.abs(ge - ge0)).item() <= 1e-10 * scale
+    off = 0
+    for p, n in enumerate(sizes):
+        n = int(n)
+        q_p = api.batched_block(q, sz, qoff, p)
+        gq_p = gq_cat[int(qoff[p]):int(qoff[p]) + n * n].view(n, n).t()
+        gd1, ge1 = api.syev_backward(lam[off:off + n].contiguous(), q_p, gl_cat[off:off + n].contiguous(), gq_p,
+                                     opts={"path": 1})
+        assert torch.equal(gd[off:off + n], gd1)
+        assert torch.equal(ge[off:off + n - 1], ge1)
+        off += n
