@@ -346,6 +346,26 @@ def context_measurements(api, _lib, lib, torch):
                                       "max_abs_lambda_diff_vs_level_launches": float((lam_p - lam).abs().max()),
                                       "launch": "one persistent kernel (after 4 memsets), captured in a CUDA graph"}
     del lam_p, q_p
+    # the same batch with the split-precision product for merges of order 256 and up
+    # (level form; the persistent kernel keeps the FP64 product)
+    plan_s = api.BatchedPlan(sizes, opts={"path": PATHS["ozaki"]})
+    lam_s, q_s = plan_s.outputs()
+    plan_s.autotune(d_cat, e_cat, lam_s, q_s)
+    plan_s.capture(d_cat, e_cat, lam_s, q_s)
+    for _ in range(2):
+        plan_s.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan_s.replay()
+    e1.record()
+    e1.synchronize()
+    ms_s = e0.elapsed_time(e1) / reps
+    ctx["batched_4096_split"] = {"ms": ms_s, "problems_per_s": 4096 / (ms_s * 1e-3),
+                                 "status_nonzero": int((plan_s.status != 0).sum()),
+                                 "max_abs_lambda_diff_vs_fp64": float((lam_s - lam).abs().max()),
+                                 "launch": "one launch per phase per tree level, captured in a CUDA graph"}
+    del plan_s, lam_s, q_s
     del plan, q, lam
     torch.cuda.empty_cache()
     ctx["backward_batched_64x4096"] = backward_measurement(api, _lib, lib, torch)
