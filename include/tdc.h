@@ -334,8 +334,7 @@ int tdc_profile_end(tdc_profile* out);
  *   held on every GPU that loads it until the process exits.  The caller passes
  *   inputs and outputs only (device pointers, as for tdc_syev_tridiag).  The first
  *   call on each device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
- *   Calls share the array: calls whose work overlaps on the GPU (different streams,
+ *   with that device current.  Calls share the array: calls whose work overlaps on the GPU (different streams,
  *   or the same array used from two host threads without ordering) race.  The call
  *   clears what must start at zero (the status word when dev_status is NULL) and
  *   calls no cudaMalloc, cudaFree or other allocating routine.
