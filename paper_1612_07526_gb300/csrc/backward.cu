@@ -250,7 +250,7 @@ extern "C" size_t tdc_backward_workspace_bytes(int64_t n, const tdc_opts* opts) 
   if (n < 1) return 0;
   size_t b = al(n * 4) + al(n * 4) + al(16) + 3 * al((size_t)n * n * 8) + al(1 << 20);
   if (bw_split(opts) && n <= INT32_MAX) {
-    const std::vector<SgProblem> pr{SgProblem{(int)n, (int)n, (int)n, nullptr, 0, 0, nullptr, 0, nullptr, 0}};
+    const std::vector<SgProblem> pr{sg_problem((int)n, (int)n, (int)n, SgOp{}, SgOp{}, nullptr, 0)};
     b += al(split_gemm_bytes(pr, bw_slices(opts)));
   }
   return b;
@@ -299,12 +299,12 @@ extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const 
       // the split-precision arena follows the FP64 path's buffers
       unsigned char* arena = b + off;
       const size_t abytes = ws_bytes > off ? ws_bytes - off : 0;
-      std::vector<SgProblem> pr{SgProblem{(int)n, s, (int)n, Q, ldq, 1, G, n, P, n}};   // P = Q^T G
+      std::vector<SgProblem> pr{sg_problem((int)n, s, (int)n, sg_dense(Q, ldq, true), sg_dense(G, n), P, n)};   // P = Q^T G
       int* err = dev_status ? dev_status : ns_dev + 1;      // a timed-out tensor-core wait sets bit 8 here
       int rc = split_gemm(pr, bw_slices(opts), arena, abytes, err, st);
       if (rc) return rc;
       k_bw_m<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P, lambda, cols, n, s, G);   // M_S into G
-      pr[0] = SgProblem{(int)n, s, (int)n, Q, ldq, 0, G, n, W, n};                      // W = Q M_S
+      pr[0] = sg_problem((int)n, s, (int)n, sg_dense(Q, ldq), sg_dense(G, n), W, n);                  // W = Q M_S
       rc = split_gemm(pr, bw_slices(opts), arena, abytes, err, st);
       if (rc) return rc;
     } else {
@@ -344,8 +344,8 @@ extern "C" size_t tdc_backward_batched_workspace_bytes(int32_t batch, const int6
     for (int p = 0; p < batch; ++p) {
       const int64_t s = max_cols < 0 ? n_host[p] : std::min<int64_t>(max_cols, n_host[p]);
       if (n_host[p] > INT32_MAX) return 0;
-      pr.push_back(SgProblem{(int)n_host[p], (int)std::max<int64_t>(s, 1), (int)n_host[p], nullptr, 0, 0, nullptr,
-                             0, nullptr, 0});
+      pr.push_back(sg_problem((int)n_host[p], (int)std::max<int64_t>(s, 1), (int)n_host[p], SgOp{}, SgOp{}, nullptr,
+                              0));
     }
     bytes += al(split_gemm_bytes(pr, bw_slices(opts)));
   }
@@ -416,8 +416,10 @@ extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n
       for (int p = 0; p < batch; ++p) {
         if (pr[p].s == 0) continue;
         const int n = (int)pr[p].n;
-        pa.push_back(SgProblem{n, pr[p].s, n, Q_cat + pr[p].q, n, 1, L.G + pr[p].g, n, L.P + pr[p].g, n});   // Q^T G
-        pw.push_back(SgProblem{n, pr[p].s, n, Q_cat + pr[p].q, n, 0, L.G + pr[p].g, n, L.W + pr[p].g, n});   // Q M
+        pa.push_back(sg_problem(n, pr[p].s, n, sg_dense(Q_cat + pr[p].q, n, true), sg_dense(L.G + pr[p].g, n),
+                                L.P + pr[p].g, n));                                                       // Q^T G
+        pw.push_back(sg_problem(n, pr[p].s, n, sg_dense(Q_cat + pr[p].q, n), sg_dense(L.G + pr[p].g, n),
+                                L.W + pr[p].g, n));                                                       // Q M
       }
       unsigned char* arena = b + off;
       const size_t abytes = ws_bytes > off ? ws_bytes - off : 0;

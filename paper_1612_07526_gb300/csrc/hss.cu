@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "tdc_hss.cuh"
+#include "tdc_ozaki.cuh"
 
 namespace tdc {
 
@@ -572,10 +573,29 @@ void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, siz
 // The largest sample an HSS merge may grow to: r + p doubled hss_grow times.
 int hss_rp_max(const tdc_opts& o) { return o.hss_rp << std::max(0, std::min(o.hss_grow, 4)); }
 
+// The split-precision GEMMs of an HSS merge (sampling, and the leaf-level products of
+// the multiply) use 7 slices: the sampled Y feeds rank decisions at the compression
+// tolerance, and 6 slices left noise of about 2e-12 relative in Y at K = 16384.
+constexpr int kHssSlices = 7;
+
+// Workspace of the split GEMMs of one HSS merge of order m (K <= m kept columns, rp
+// samples, leaves of at most hss_leaf): the larger of the sampling batch (Qhat Omega1,
+// Qhat^T Omega2) and a leaf batch (X(:, t) D_t or X(:, t) U_t for every leaf t).
+static size_t hss_split_bytes(int64_t m, const tdc_opts& o, int rp) {
+  const int hl = std::max(o.hss_leaf, 2);
+  std::vector<SgProblem> sampling(2, sg_problem((int)m, rp, (int)m, SgOp{}, SgOp{}, nullptr, 0));
+  std::vector<SgProblem> leaves;
+  for (int64_t lo = 0; lo < m; lo += hl) {
+    const int sz = (int)std::min<int64_t>(hl, m - lo);
+    leaves.push_back(sg_problem((int)m, std::max(sz, rp), sz, SgOp{}, SgOp{}, nullptr, 0));
+  }
+  return std::max(split_gemm_bytes(sampling, kHssSlices), split_gemm_bytes(leaves, kHssSlices));
+}
+
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o) {
   HssLayout L;
   hss_layout(L, nullptr, (int)m, (int)m, o, hss_rp_max(o));   // every layout fits in the largest
-  return L.bytes + 4096;
+  return L.bytes + 4096 + hss_split_bytes(m, o, hss_rp_max(o)) + 256;
 }
 
 // 1 in *flag if a node's row or column ID used all rp samples while it had more rows
@@ -614,10 +634,15 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   std::vector<std::vector<int>> byl;
   // Algorithm 1 with r + p = rp sample columns, then the check of the ID ranks against
   // the sample count.  Returns 0, kHssSaturated, 3 or 4.
+  unsigned char* split_ws = nullptr;       // the split GEMMs' workspace, after the layout
+  size_t split_bytes = 0;
   auto compress = [&]() -> int {
     rmax = std::max(std::max(o.hss_leaf, 2), 2 * rp);
     hss_layout(L, arena, K, m, o, rp);
     if (L.bytes > arena_bytes) return 3;
+    const size_t so = (L.bytes + 4095) & ~size_t(255);
+    split_ws = arena + so;
+    split_bytes = arena_bytes > so ? arena_bytes - so : 0;
     nn = (int)L.tree.size();
     const auto& tree = L.tree;
     auto& nd = L.nd;
@@ -635,17 +660,17 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om1, K, rp, seed, 1);
     k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om2, K, rp, seed, 2);
     k_hss_cols<<<grid_cap(K / 256 + 1, 4), 256, 0, st>>>(hJ, w, xc);
-    {
-      std::vector<HGemm> g(2, gemm0());
-      g[0].M = K; g[0].N = rp; g[0].K = K;
-      g[0].a.mode = HOP_QHAT;
-      g[0].b.mode = HOP_DENSE; g[0].b.p = L.om1; g[0].b.ld = K;
-      g[0].C = L.Y; g[0].ldc = K;
-      g[1] = g[0];
-      g[1].a.mode = HOP_QHAT_T;
-      g[1].b.p = L.om2;
-      g[1].C = L.Z;
-      launch_gemms(g, tab, toff, q, xc, st);
+    {                                           // on the split-precision tensor-core GEMM
+      SgOp qa;
+      qa.mode = SG_QHAT;
+      qa.wcol = q.wcol;
+      qa.sinv = q.sinv;
+      SgOp qt = qa;
+      qt.mode = SG_QHAT_T;
+      std::vector<SgProblem> g{sg_problem(K, rp, K, qa, sg_dense(L.om1, K), L.Y, K),
+                               sg_problem(K, rp, K, qt, sg_dense(L.om2, K), L.Z, K)};
+      const int rc = split_gemm(g, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
+      if (rc) return rc == 3 ? 3 : 4;
     }
     // ---- leaves: Phi = Y(t) - D Omega1(t), Theta = Z(t) - D^T Omega2(t), in place
     maxlev = 0;
@@ -752,22 +777,35 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   phase_mark(12, true, 0, st);
 
   // ---- multiply: Out = X Qhat_hss, X = Q_sel (m rows, K kept columns)
+  SgOp xo;                                  // gathered columns of Q_sel (kept order)
+  xo.mode = SG_XCOLS;
+  xo.xcol = xc.col;
+  xo.xlo = xc.lo;
+  xo.xhi = xc.hi;
   for (int lev = maxlev; lev >= 1; --lev) {   // up-sweep: G = X(:, t) U, G_p = [G_1 G_2] U_p
     std::vector<HGemm> g;
+    std::vector<SgProblem> gl;                // leaves: on the split-precision GEMM
     for (int i : byl[lev]) {
+      if (nd[i].leaf) {
+        SgOp xa = xo;
+        xa.c0 = tree[i].lo;
+        SgProblem p = sg_problem(m, rp, tree[i].hi - tree[i].lo, xa, sg_dense(nd[i].U, rmax), nd[i].G, m);
+        p.Ndev = nd[i].kU;
+        gl.push_back(p);
+        continue;
+      }
       HGemm a = gemm0();
       a.M = m; a.N = rp; a.Ndev = nd[i].kU;
       a.C = nd[i].G; a.ldc = m;
       a.b.mode = HOP_DENSE; a.b.p = nd[i].U; a.b.ld = rmax;
-      if (nd[i].leaf) {
-        a.K = tree[i].hi - tree[i].lo;
-        a.a.mode = HOP_XCOLS; a.a.c0 = tree[i].lo;
-      } else {
-        a.K = 2 * rp; a.Kdev = nd[i].rows_u;
-        a.a.mode = HOP_STACK; a.a.p = nd[tree[i].c1].G; a.a.ld = m;
-        a.a.p2 = nd[tree[i].c2].G; a.a.ld2 = m; a.a.split = nd[tree[i].c1].kU;
-      }
+      a.K = 2 * rp; a.Kdev = nd[i].rows_u;
+      a.a.mode = HOP_STACK; a.a.p = nd[tree[i].c1].G; a.a.ld = m;
+      a.a.p2 = nd[tree[i].c2].G; a.a.ld2 = m; a.a.split = nd[tree[i].c1].kU;
       g.push_back(a);
+    }
+    if (!gl.empty()) {
+      const int rc = split_gemm(gl, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
+      if (rc) return rc == 3 ? 3 : 4;
     }
     launch_gemms(g, tab, toff, q, xc, st);
   }
@@ -799,16 +837,23 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     launch_gemms(g2, tab, toff, q, xc, st);
   }
   {                                             // leaves: Out(:, pos(t)) = X(:, t) D + F V^T
-    std::vector<HGemm> g1, g2;
+    std::vector<HGemm> g2;
+    std::vector<SgProblem> g1;                  // X(:, t) D_t on the split-precision GEMM
     for (int i = 0; i < nn; ++i) {
       if (!nd[i].leaf) continue;
       const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
-      HGemm a = gemm0();
-      a.M = m; a.N = sz; a.K = sz;
-      a.a.mode = HOP_XCOLS; a.a.c0 = lo;
-      a.b.mode = HOP_QHAT; a.b.r0 = lo; a.b.c0 = lo;
-      a.cmode = HC_PTRS; a.cptrs = outp; a.cc0 = lo;
-      g1.push_back(a);
+      SgOp xa = xo;
+      xa.c0 = lo;
+      SgOp db;
+      db.mode = SG_QHAT;
+      db.r0 = lo;
+      db.c0 = lo;
+      db.wcol = q.wcol;
+      db.sinv = q.sinv;
+      SgProblem p = sg_problem(m, sz, sz, xa, db, nullptr, 0);
+      p.cptrs = outp;
+      p.cc0 = lo;
+      g1.push_back(p);
       if (nn > 1) {
         HGemm b = gemm0();
         b.M = m; b.N = sz; b.K = rp; b.Kdev = nd[i].kV;
@@ -819,7 +864,8 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
         g2.push_back(b);
       }
     }
-    launch_gemms(g1, tab, toff, q, xc, st);
+    const int rc = split_gemm(g1, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
+    if (rc) return rc == 3 ? 3 : 4;
     launch_gemms(g2, tab, toff, q, xc, st);
   }
   phase_mark(12, false, 4 * maxlev + 2, st);

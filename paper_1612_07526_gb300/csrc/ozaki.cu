@@ -839,15 +839,33 @@ int64_t job_ldk(const MergeJob& J) { return rup((int64_t)J.n1 + J.n2 + 3 * kOzPa
 // kernel forms the 128 x 64 tiles.  Used for the backward's products.
 struct SgJob {                       // CUtensorMap members force 64-byte alignment
   CUtensorMap mapA, mapB;            // slices: [slice][k / 32][row or column][32]
-  const double* a;                   // A[r, k] = a[r + k lda] (atrans 0) or a[k + r lda] (atrans 1)
-  const double* b;                   // B[k, c] = b[k + c ldb]
-  double* C;                         // C[r, c] = C[r + c ldc]
+  SgOp a, b;                         // A (M x K) and B (K x N), element by element
+  double* C;                         // C[r, c] = C[r + c ldc], or cptrs[cc0 + c][r]
+  double* const* cptrs;
+  const int* Ndev;                   // actual column count (device), or null
   uint16_t *as, *bs;
   int32_t *aexp, *bexp;              // INT32_MIN: a zero row / column
-  int64_t lda, ldb, ldc;
+  int64_t ldc;
   int32_t M, N, K, Kp;               // Kp: K rounded up to 64
-  int32_t atrans, pad_;
+  int32_t cc0, pad_;
 };
+
+// Element (row, col) of an operand in one of the SG_* forms.
+__device__ __forceinline__ double sg_at(const SgOp& o, int row, int col) {
+  switch (o.mode) {
+    case SG_DENSE: return o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld];
+    case SG_DENSE_T: return o.p[(int64_t)(o.c0 + col) + (int64_t)(o.r0 + row) * o.ld];
+    case SG_QHAT: return o.wcol[o.c0 + col][o.r0 + row] * o.sinv[o.c0 + col];
+    case SG_QHAT_T: return o.wcol[o.r0 + row][o.c0 + col] * o.sinv[o.r0 + row];
+    case SG_XCOLS: {
+      const int j = o.c0 + col;
+      return row >= o.xlo[j] && row < o.xhi[j] ? o.xcol[j][row] : 0.0;
+    }
+    default: return 0.0;
+  }
+}
+// whether consecutive rows of the operand are adjacent in memory (else consecutive columns)
+__device__ __forceinline__ bool sg_rows_contiguous(int mode) { return mode != SG_DENSE_T && mode != SG_QHAT_T; }
 
 // rows of A, 32 per block: the row's power of two, then its digits, 64 k at a time
 // through shared memory; lanes run along whichever index is contiguous in memory
@@ -864,11 +882,12 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   const int M = J.M, K = J.K;
   auto at = [&](int r, int k) -> double {          // A[r0 + r, k], zero outside
     if (r0 + r >= M || k >= K) return 0.0;
-    return J.atrans ? J.a[(int64_t)k + (int64_t)(r0 + r) * J.lda] : J.a[(int64_t)(r0 + r) + (int64_t)k * J.lda];
+    return sg_at(J.a, r0 + r, k);
   };
+  const bool rowc = sg_rows_contiguous(J.a.mode);
   // pass 1: row maxima on the magnitude bits
   unsigned long long mx = 0ull;
-  if (!J.atrans) {
+  if (rowc) {
     const int r = tid & 31, kq = tid >> 5;
     for (int k = kq; k < K; k += 8) {
       const unsigned long long v = (unsigned long long)__double_as_longlong(at(r, k)) & 0x7FFFFFFFFFFFFFFFull;
@@ -909,7 +928,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   const int wr = tid >> 3, wk = (tid & 7) * 8;
   const int shift = 8 * S - 1 - s_exp[wr];
   for (int k0 = 0; k0 < J.Kp; k0 += 64) {
-    if (!J.atrans) {
+    if (rowc) {
       const int r = tid & 31, kq = tid >> 5;
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) tile[kq * 8 + kk][r] = at(r, k0 + kq * 8 + kk);
@@ -954,10 +973,11 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
   const int lane = threadIdx.x & 31;
   const int c = (int)(blockIdx.x - cum[jb]) * 8 + (int)(threadIdx.x >> 5);
   if (c >= J.N) return;                             // uniform over the warp
-  const double* col = J.b + (int64_t)c * J.ldb;
+  const bool live = !J.Ndev || c < *J.Ndev;         // columns past the actual count are zero
+  auto at = [&](int k) -> double { return live && k < J.K ? sg_at(J.b, k, c) : 0.0; };
   unsigned long long m = 0ull;
   for (int k = lane; k < J.K; k += 32) {
-    const unsigned long long v = (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long v = (unsigned long long)__double_as_longlong(at(k)) & 0x7FFFFFFFFFFFFFFFull;
     m = v > m ? v : m;
   }
 #pragma unroll
@@ -975,7 +995,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       uint16_t t[S];
-      digits_bf16<S>(round_scaled(k0 + j < J.K ? col[k0 + j] : 0.0, shift), t);
+      digits_bf16<S>(round_scaled(at(k0 + j), shift), t);
 #pragma unroll
       for (int p = 0; p < S; ++p) dg[j][p] = t[p];
     }
@@ -1225,15 +1245,17 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
       }
       if (!ok) break;
       const int grow = T.row0 + row;
+      const int ncol = J.Ndev ? min(*J.Ndev, J.N) : J.N;
       if (grow < J.M) {
         const int ea = J.aexp[grow];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = T.ct * kOzBN + half * 32 + j;
-          if (col < J.N) {
+          if (col < ncol) {
             const int eb = J.bexp[col];
-            J.C[(int64_t)grow + (int64_t)col * J.ldc] =
-                (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
+            const double x = (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
+            if (J.cptrs) J.cptrs[J.cc0 + col][grow] = x;
+            else J.C[(int64_t)grow + (int64_t)col * J.ldc] = x;
           }
         }
       }
@@ -1358,12 +1380,12 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
     J.K = p.K;
     J.Kp = (int32_t)rup(p.K, 64);
     J.a = p.a;
-    J.lda = p.lda;
-    J.atrans = p.atrans;
     J.b = p.b;
-    J.ldb = p.ldb;
     J.C = p.C;
     J.ldc = p.ldc;
+    J.cptrs = p.cptrs;
+    J.cc0 = p.cc0;
+    J.Ndev = p.Ndev;
     J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
     J.bs = reinterpret_cast<uint16_t*>(take((size_t)S * p.N * J.Kp * 2));
     J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));
@@ -1392,7 +1414,7 @@ int split_gemm(const std::vector<SgProblem>& pr, int slices, unsigned char* ws, 
                cudaStream_t st) {
   if (pr.empty()) return 0;
   for (const SgProblem& p : pr)
-    if (p.M < 1 || p.N < 1 || p.K < 1 || !p.a || !p.b || !p.C) return -1;
+    if (p.M < 1 || p.N < 1 || p.K < 1 || (!p.C && !p.cptrs)) return -1;
   if (ws_bytes < split_gemm_bytes(pr, slices)) return 3;
   switch (slices < 5 ? 5 : (slices > 7 ? 7 : slices)) {
     case 5: return split_gemm_s<5>(pr, ws, ws_bytes, dev_err, st);

@@ -57,23 +57,61 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
 // bf16 slice products per FP64-equivalent product: pairs (p, q) with p + q <= S + 2.
 int oz_slice_pairs(int slices);
 
-// Dense products C = A B on the same split-precision tensor-core path (the backward's
-// Q^T G and Q M): A is M x K, column-major with leading dimension lda, or given as its
-// transpose (atrans: A[r, k] = a[k + r lda]); B is K x N column-major; C is M x N
-// column-major and is overwritten.  One call runs a batch: slicing of every A and B,
-// then one persistent GEMM over all their tiles.  The workspace holds the slices
-// (about 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives
-// its size.  Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
-struct SgProblem {
-  int M, N, K;
-  const double* a;
-  int64_t lda;
-  int atrans;
-  const double* b;
-  int64_t ldb;
-  double* C;
-  int64_t ldc;
+// Products C = A B on the same split-precision tensor-core path (the backward's Q^T G and
+// Q M; the HSS sampling and leaf-level products).  An operand is read element by element
+// through one of these forms, (row, column) of the operand as the product uses it:
+//   SG_DENSE     p[(r0 + row) + (c0 + col) ld]            (column-major)
+//   SG_DENSE_T   p[(c0 + col) + (r0 + row) ld]            (the transpose of a column-major array)
+//   SG_QHAT      wcol[c0 + col][r0 + row] sinv[c0 + col]  (the merge's Cauchy factor, generated)
+//   SG_QHAT_T    wcol[r0 + row][c0 + col] sinv[r0 + row]  (its transpose)
+//   SG_XCOLS     xcol[c0 + col][row] for xlo[c0 + col] <= row < xhi[c0 + col], else 0
+//                (gathered eigenvector columns with their nonzero row ranges)
+// B is read as (k, column); its forms are SG_DENSE, SG_QHAT and SG_XCOLS.  C (M x N) is
+// overwritten, column-major with ldc, or through column pointers cptrs[cc0 + col][row].
+// Ndev (optional, device) holds the actual column count (<= N): B's further columns count
+// as zero and C's are not written.  One call runs a batch: slicing of every A and B, then
+// one persistent GEMM over all their tiles.  The workspace holds the slices (about
+// 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives its size.
+// Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
+enum : int { SG_DENSE = 0, SG_DENSE_T = 1, SG_QHAT = 2, SG_QHAT_T = 3, SG_XCOLS = 4 };
+struct SgOp {
+  int mode = SG_DENSE;
+  int r0 = 0, c0 = 0;
+  const double* p = nullptr;
+  int64_t ld = 0;
+  double* const* wcol = nullptr;
+  const double* sinv = nullptr;
+  const double* const* xcol = nullptr;
+  const int32_t* xlo = nullptr;
+  const int32_t* xhi = nullptr;
 };
+struct SgProblem {
+  int M = 0, N = 0, K = 0;
+  SgOp a, b;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double* const* cptrs = nullptr;
+  int cc0 = 0;
+  const int* Ndev = nullptr;
+};
+inline SgOp sg_dense(const double* p, int64_t ld, bool trans = false) {
+  SgOp o;
+  o.mode = trans ? SG_DENSE_T : SG_DENSE;
+  o.p = p;
+  o.ld = ld;
+  return o;
+}
+inline SgProblem sg_problem(int M, int N, int K, SgOp a, SgOp b, double* C, int64_t ldc) {
+  SgProblem p;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.a = a;
+  p.b = b;
+  p.C = C;
+  p.ldc = ldc;
+  return p;
+}
 size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices);
 int split_gemm(const std::vector<SgProblem>& pr, int slices, unsigned char* ws, size_t ws_bytes, int* dev_err,
                cudaStream_t st);
