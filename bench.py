@@ -227,9 +227,9 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
         out["split_operand_split_ms"] = p.ms[9]
         out["split_gemm_bf16_tflops"] = p.split_tensor_flops / (p.ms[8] * 1e-3) / 1e12
     out["phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES)}
-    if p.ms[10] > 0:                 # HSS: the sampling GEMMs' FP64 rate (exact flops 4 K^2 (r + p))
+    if p.ms[10] > 0:                 # HSS: the sampling's FP64-equivalent rate (4 K^2 (r + p) flops, split GEMM)
         out["hss"] = {"sampling_flops": p.hss_sampling_flops,
-                      "sampling_fp64_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
+                      "sampling_fp64_equivalent_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
                       "regrowths": int(p.hss_regrowths), "dense_fallbacks": int(p.hss_fallbacks)}
     out["K_total"] = int(p.K_total)
     out["accuracy"] = sampled_accuracy(torch, d, e, lam, q)
@@ -272,8 +272,8 @@ def context_measurements(api, _lib, lib, torch):
     ctx["toeplitz_16384_fp64"] = profiled_solve(api, _lib, lib, torch, d, e, "fp64", exact=ex)
     ctx["toeplitz_16384_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", exact=ex)
     ctx["toeplitz_16384_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss", exact=ex)
-    # HSS with 256-leaves and 64 starting samples (grown where a rank reaches them): fewer
-    # FP64 flops in the sampling and the leaf blocks of the multiply, a looser residual
+    # HSS with 256-leaves and 64 starting samples (grown where a rank reaches them): less
+    # work in the sampling and the IDs, a looser residual
     ctx["toeplitz_16384_hss_leaf256_rp64"] = profiled_solve(api, _lib, lib, torch, d, e, "hss", exact=ex,
                                                             hss_leaf=256, hss_rp=64)
     d, e = W.normal_tridiag(16384, 0)
