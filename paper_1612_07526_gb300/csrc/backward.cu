@@ -17,7 +17,7 @@
 #include <vector>
 
 #include "../../include/tdc.h"
-#include "tdc_hss.cuh"
+#include "tdc_dgemm.cuh"
 #include "tdc_internal.cuh"
 #include "tdc_ozaki.cuh"
 
@@ -308,19 +308,18 @@ extern "C" int tdc_syev_tridiag_backward(int64_t n, const double* lambda, const 
       rc = split_gemm(pr, bw_slices(opts), arena, abytes, err, st);
       if (rc) return rc;
     } else {
-      std::vector<HGemm> g(1);
-      std::memset(g.data(), 0, sizeof(HGemm));
+      std::vector<DGemm> g(1);
+      std::memset(g.data(), 0, sizeof(DGemm));
       g[0].M = (int)n; g[0].N = s; g[0].K = (int)n;          // P = Q^T G
-      g[0].a.mode = HOP_DENSE_T; g[0].a.p = Q; g[0].a.ld = ldq;
-      g[0].b.mode = HOP_DENSE; g[0].b.p = G; g[0].b.ld = n;
+      g[0].a = DMat{Q, ldq, 1};
+      g[0].b = DMat{G, n, 0};
       g[0].C = P; g[0].ldc = n; g[0].alpha = 1.0;
       size_t toff = 0;
-      launch_dense_gemms(g, tab, toff, st);
+      if (launch_dgemms(g, tab, toff, 1 << 20, st)) return 3;
       k_bw_m<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P, lambda, cols, n, s, G);   // M_S into G
-      g[0].a.mode = HOP_DENSE; g[0].a.p = Q; g[0].a.ld = ldq;                            // W = Q M_S
-      g[0].b.p = G;
+      g[0].a = DMat{Q, ldq, 0};                                                           // W = Q M_S
       g[0].C = W;
-      launch_dense_gemms(g, tab, toff, st);
+      if (launch_dgemms(g, tab, toff, 1 << 20, st)) return 3;
     }
   }
   k_bw_band<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Q, ldq, n, lambda, g_lambda, W, cols, s, g_d, g_e);
@@ -433,28 +432,27 @@ extern "C" int tdc_syev_tridiag_backward_batched(int32_t batch, const int64_t* n
                                                                  L.W, L.cols, g_d_cat, g_e_cat);
       return cudaGetLastError() == cudaSuccess ? 0 : 4;
     }
-    std::vector<HGemm> g;
+    std::vector<DGemm> g;
     for (int p = 0; p < batch; ++p) {           // P = Q^T G
       if (pr[p].s == 0) continue;
-      HGemm h;
+      DGemm h;
       std::memset(&h, 0, sizeof(h));
       h.M = (int)pr[p].n; h.N = pr[p].s; h.K = (int)pr[p].n;
-      h.a.mode = HOP_DENSE_T; h.a.p = Q_cat + pr[p].q; h.a.ld = pr[p].n;
-      h.b.mode = HOP_DENSE; h.b.p = L.G + pr[p].g; h.b.ld = pr[p].n;
+      h.a = DMat{Q_cat + pr[p].q, pr[p].n, 1};
+      h.b = DMat{L.G + pr[p].g, pr[p].n, 0};
       h.C = L.P + pr[p].g; h.ldc = pr[p].n; h.alpha = 1.0;
       g.push_back(h);
     }
     size_t toff = 0;
-    if (g.size() * sizeof(HGemm) + (g.size() + 1) * 8 + 1024 > kBwTab / 2) return 3;
-    launch_dense_gemms(g, L.tab, toff, st);
+    if (launch_dgemms(g, L.tab, toff, kBwTab, st)) return 3;
     k_bwb_m<<<gb, 256, 0, st>>>(L.prob, batch, cum_ns, ns, L.P, lambda_cat, L.cols, L.G);   // M into G
-    for (HGemm& h : g) {                         // W = Q M: same shapes, same offsets
+    for (DGemm& h : g) {                         // W = Q M: same shapes, same offsets
       const int64_t go = h.C - L.P;
-      h.a.mode = HOP_DENSE;
+      h.a.trans = 0;
       h.b.p = L.G + go;
       h.C = L.W + go;
     }
-    launch_dense_gemms(g, L.tab, toff, st);
+    if (launch_dgemms(g, L.tab, toff, kBwTab, st)) return 3;
   }
   k_bwb_band<<<(unsigned)((vtot + 255) / 256), 256, 0, st>>>(L.prob, batch, cum_n, vtot, Q_cat, g_lambda_cat,
                                                              L.W, L.cols, g_d_cat, g_e_cat);

@@ -3,14 +3,19 @@
 // interpolative decompositions, then U = Q_sel Qhat_hss is formed with an up-sweep
 // through the nested bases U, the sibling couplings B and a down-sweep through V.
 // Qhat stays in the order of the sorted d (no Gu grouping: it would break the
-// off-diagonal low rank).  Everything runs in FP64:
+// off-diagonal low rank).  The decompositions run in FP64:
 //   k_hss_omega   Gaussian sampling matrices (SplitMix64 + Box-Muller)
-//   k_hss_gemm    batched FP64 GEMM whose operands may be dense, transposed,
-//                 Qhat blocks generated on the fly, gathered columns of Q_sel, or two
-//                 stacked blocks; the output may be scattered to eigenvector columns
-//   k_hss_id      batched column-pivoted QR of Phi^T: row ID Phi ~= U Phi(I, :)
+//   k_hss_id_cl   column-pivoted QR of Phi^T (row ID Phi ~= U Phi(I, :)), one
+//                 cluster of 8 CTAs per decomposition with Phi^T held in their
+//                 shared memory; k_hss_id, one CTA and global scratch, where it
+//                 does not fit
 //   k_hss_parent  per parent: sibling couplings B and the parent's Phi, Theta
-//   k_hss_hat     per parent: Yhat = V^T [Yhat_1; Yhat_2], Zhat = U^T [Zhat_1; Zhat_2]
+//   k_hss_skel    global skeleton indices
+// Every product runs on the split-precision tensor-core GEMM (tdc_ozaki.cuh, 7 slices):
+// the sampling Y = Qhat Omega1 and Z = Qhat^T Omega2 with Qhat's diagonal leaf blocks
+// read as zero, the nodes' Yhat = V^T [Yhat_1; Yhat_2] and Zhat = U^T [Zhat_1; Zhat_2],
+// and the multiply's up-sweep, couplings, down-sweep and leaf products.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,113 +38,6 @@ struct QhatSrc {
 };
 __device__ __forceinline__ double qhat(const QhatSrc& q, int j, int i) {
   return q.wcol[i][j] * q.sinv[i];
-}
-
-// ------------------------------------------------------------------ batched GEMM
-__device__ __forceinline__ double fetch(const HOp& op, const QhatSrc& q, const HssCols& xc, int r, int c) {
-  switch (op.mode) {
-    case HOP_DENSE: return op.p[(int64_t)(op.c0 + c) * op.ld + op.r0 + r];
-    case HOP_DENSE_T: {
-      const int c0 = op.c0 + (op.row_off_dev ? *op.row_off_dev : 0);
-      return op.p[(int64_t)(op.r0 + r) * op.ld + c0 + c];
-    }
-    case HOP_QHAT: {
-      const int j = op.ridx ? op.ridx[r] : op.r0 + r;
-      const int i = op.cidx ? op.cidx[c] : op.c0 + c;
-      return qhat(q, j, i);
-    }
-    case HOP_QHAT_T: {
-      const int j = op.cidx ? op.cidx[c] : op.c0 + c;
-      const int i = op.ridx ? op.ridx[r] : op.r0 + r;
-      return qhat(q, j, i);
-    }
-    case HOP_XCOLS: {
-      const int j = op.c0 + c;                 // kept (sorted-d) column index
-      return r >= xc.lo[j] && r < xc.hi[j] ? xc.col[j][r] : 0.0;
-    }
-    case HOP_STACK: {                          // columns [0, k1) from p, the rest from p2
-      const int k1 = *op.split;
-      return c < k1 ? op.p[(int64_t)c * op.ld + r] : op.p2[(int64_t)(c - k1) * op.ld2 + r];
-    }
-    case HOP_STACK_ROWS: {                     // rows [0, k1) from p, the rest from p2
-      const int k1 = *op.split;
-      return r < k1 ? op.p[(int64_t)c * op.ld + r] : op.p2[(int64_t)c * op.ld2 + (r - k1)];
-    }
-    default: return 0.0;
-  }
-}
-
-constexpr int TB = 64, TK = 16;
-
-// Whether consecutive k of an operand are adjacent in memory (then the tile loader
-// walks k fastest across threads, else the row / column index), so that a warp's loads
-// fall on few cache lines.  A is read as a(r, k), B as b(k, c).
-__device__ __forceinline__ bool a_k_contiguous(int mode) { return mode == HOP_DENSE_T || mode == HOP_QHAT_T; }
-__device__ __forceinline__ bool b_k_contiguous(int mode) { return mode != HOP_DENSE_T && mode != HOP_QHAT_T; }
-
-__global__ __launch_bounds__(256) void k_hss_gemm(const HGemm* __restrict__ jobs, int njobs,
-                                                  const int64_t* __restrict__ cum, QhatSrc q, HssCols xc) {
-  __shared__ double As[TK][TB + 1];
-  __shared__ double Bs[TK][TB + 1];
-  const int jb = find_job(cum, njobs, blockIdx.x);
-  const HGemm G = jobs[jb];
-  const int64_t t = blockIdx.x - cum[jb];
-  const int M = G.Mdev ? *G.Mdev : G.M;
-  const int N = G.Ndev ? *G.Ndev : G.N;
-  const int Kd = G.Kdev ? *G.Kdev : G.K;
-  const int ntm = (G.M + TB - 1) / TB;
-  const int tm = (int)(t % ntm), tn = (int)(t / ntm);
-  const int r0 = tm * TB, c0 = tn * TB;
-  if (r0 >= M || c0 >= N) return;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  const bool ak = a_k_contiguous(G.a.mode), bk = b_k_contiguous(G.b.mode);   // uniform per job
-  for (int k0 = 0; k0 < Kd; k0 += TK) {
-    for (int e = tid; e < TK * TB; e += 256) {
-      const int kk = ak ? e % TK : e / TB, rr = ak ? e / TK : e % TB;
-      const int r = r0 + rr, k = k0 + kk;
-      As[kk][rr] = (r < M && k < Kd) ? fetch(G.a, q, xc, r, k) : 0.0;
-    }
-    for (int e = tid; e < TK * TB; e += 256) {
-      const int kk = bk ? e % TK : e / TB, cc = bk ? e / TK : e % TB;
-      const int c = c0 + cc, k = k0 + kk;
-      Bs[kk][cc] = (c < N && k < Kd) ? fetch(G.b, q, xc, k, c) : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-      double fa[4], fb[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) fa[a] = As[kk][tx + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) fb[b] = Bs[kk][ty + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(fa[a], fb[b], acc[a][b]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int c = c0 + ty + 16 * b;
-    if (c >= N) continue;
-    double* col;
-    if (G.cmode == HC_SCATTER) col = G.C + (int64_t)G.cpos[G.cc0 + c] * G.ldc;
-    else if (G.cmode == HC_PTRS) col = G.cptrs[G.cc0 + c];
-    else col = G.C + (int64_t)c * G.ldc;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int r = r0 + tx + 16 * a;
-      if (r >= M) continue;
-      const double v = G.alpha * acc[a][b];
-      col[r] = G.beta == 0.0 ? v : v + G.beta * col[r];
-    }
-  }
 }
 
 // ------------------------------------------------------------------ sampling matrices
@@ -310,6 +208,247 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
   }
 }
 
+// The same row ID on a cluster of kIdCluster CTAs.  CTA q of the cluster holds the
+// columns [q W, q W + W) of M = Phi^T (rows of Phi) in its shared memory (column c
+// at M + c ldm, rows 0..rp-1), so every step works on shared memory only:
+//   1. each CTA offers its unselected column of largest remaining norm; after a
+//      cluster barrier every CTA picks the same pivot p from the kIdCluster offers
+//      (largest norm, then smallest index);
+//   2. the CTA that holds p forms the Householder vector of M(k:, p) from the exact
+//      norm of that column (which also decides the stop: |R_kk| <= tol |R_00|) and
+//      publishes it in its shared memory; after a second barrier every CTA copies it;
+//   3. every CTA reflects its unselected columns (four threads per column) and
+//      downdates their squared norms by R(k, c)^2, recomputing a norm exactly when
+//      the downdate has cancelled it to 2^-26 of its last exact value or below (the
+//      usual safeguard of pivoted QR with norm downdating).
+// The pivot columns are not moved: R11 = M(0:rank, piv) is written to global scratch
+// (row-major), and after a third barrier each CTA solves R11 T(:, c) = M(0:rank, c)
+// for its other columns and writes its rows of U.
+constexpr int kIdCluster = 8;
+constexpr int kIdThreads = 256;
+
+struct IdClShape {
+  int W, ldm;                 // columns per CTA (a multiple of 8), leading dimension of M
+  size_t smem;
+};
+IdClShape id_cl_shape(int rows_max, int rp) {
+  IdClShape sh;
+  sh.W = ((rows_max + kIdCluster - 1) / kIdCluster + 7) / 8 * 8;
+  sh.ldm = (rp + 15) / 16 * 16 + 4;          // 4 mod 16 doubles: a warp's quads spread over the banks
+  sh.smem = (size_t)sh.W * sh.ldm * 8 + (size_t)2 * sh.W * 8 + (size_t)rp * 8 + (size_t)(4 + rp) * 8 +
+            (size_t)rp * 4 + (size_t)sh.W * 4 + 64;
+  return sh;
+}
+
+__global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads, 1)
+    k_hss_id_cl(const HIdJob* __restrict__ jobs, double tol, int rp, int W, int ldm) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) double sm_id[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const HIdJob Jb = jobs[blockIdx.x / kIdCluster];
+  const int rows = Jb.rows_dev ? *Jb.rows_dev : Jb.rows;
+  double* M = sm_id;                          // W x ldm
+  double* nrm = M + (size_t)W * ldm;          // downdated squared norms of M(k:, c)
+  double* nref = nrm + W;                     // the same at their last exact computation
+  double* v = nref + W;                       // this step's Householder vector (rows k..rp-1)
+  double* pub = v + rp;                       // published by the pivot's CTA: beta, r0, stop, -, v
+  int* piv = reinterpret_cast<int*>(pub + 4 + rp);
+  int* stc = piv + rp;                        // per column: -2 absent, -1 active, else its step
+  __shared__ double s_wv[kIdThreads / 32];
+  __shared__ int s_wi[kIdThreads / 32];
+  __shared__ double s_offer_v;
+  __shared__ int s_offer_i;
+  __shared__ int s_p;
+  const int tid = threadIdx.x, NT = kIdThreads;
+  const int quad = tid >> 2, ql = tid & 3, NQ = NT / 4;
+  const int g0 = crank * W;
+
+  for (int e = tid; e < W * rp; e += NT) {    // M(r, c) = Phi(g0 + c, r)
+    const int c = e % W, r = e / W, g = g0 + c;
+    M[(size_t)c * ldm + r] = g < rows ? Jb.phi[(int64_t)r * Jb.ld + g] : 0.0;
+  }
+  __syncthreads();
+  for (int c = quad; c < W; c += NQ) {        // W is a multiple of 8: uniform per warp
+    double s = 0.0;
+    for (int r = ql; r < rp; r += 4) s = fma(M[(size_t)c * ldm + r], M[(size_t)c * ldm + r], s);
+    s += __shfl_xor_sync(kFullMask, s, 1);
+    s += __shfl_xor_sync(kFullMask, s, 2);
+    if (ql == 0) {
+      nrm[c] = s;
+      nref[c] = s;
+      stc[c] = g0 + c < rows ? -1 : -2;
+    }
+  }
+  __syncthreads();
+
+  const int kmax = min(rp, rows);
+  int rank = kmax;
+  double r0 = 0.0;
+  for (int k = 0; k < kmax; ++k) {
+    // 1. this CTA's offer
+    double bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int c = tid; c < W; c += NT)
+      if (stc[c] == -1 && nrm[c] > bv) { bv = nrm[c]; bi = g0 + c; }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_xor_sync(kFullMask, bv, off);
+      const int oi = __shfl_xor_sync(kFullMask, bi, off);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { s_wv[tid >> 5] = bv; s_wi[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 1; q < NT / 32; ++q)
+        if (s_wv[q] > bv || (s_wv[q] == bv && s_wi[q] < bi)) { bv = s_wv[q]; bi = s_wi[q]; }
+      s_offer_v = bv;
+      s_offer_i = bi;
+    }
+    cl.sync();                                // offers published
+    if (tid == 0) {
+      double pv = -1.0;
+      int pi = 0x7fffffff;
+      for (int q = 0; q < kIdCluster; ++q) {
+        const double ov = *cl.map_shared_rank(&s_offer_v, q);
+        const int oi = *cl.map_shared_rank(&s_offer_i, q);
+        if (ov > pv || (ov == pv && oi < pi)) { pv = ov; pi = oi; }
+      }
+      s_p = pi;
+    }
+    __syncthreads();
+    const int p = s_p;                        // the same in every CTA
+    if (p == 0x7fffffff) { rank = k; break; }
+    const int owner = p / W;
+    // 2. the pivot's CTA: Householder vector of M(k:, p)
+    if (crank == owner && tid < 32) {
+      const int lane = tid;
+      double* col = M + (size_t)(p - g0) * ldm;
+      double s = 0.0;
+      for (int r = k + lane; r < rp; r += 32) s = fma(col[r], col[r], s);
+      s = warp_sum(s);
+      const double pn = sqrt(s);
+      const double rr0 = k == 0 ? pn : r0;
+      const bool stop = !(pn > tol * rr0);
+      double beta = 0.0;
+      if (!stop) {
+        const double alpha = col[k] >= 0.0 ? -pn : pn;
+        double vv = 0.0;
+        for (int r = k + lane; r < rp; r += 32) {
+          const double vr = col[r] - (r == k ? alpha : 0.0);
+          pub[4 + r] = vr;
+          vv = fma(vr, vr, vv);
+        }
+        vv = warp_sum(vv);
+        beta = vv > 0.0 ? 2.0 / vv : 0.0;
+        __syncwarp();                         // every lane has read col[k]
+        for (int r = k + lane; r < rp; r += 32) col[r] = r == k ? alpha : 0.0;
+        if (lane == 0) stc[p - g0] = k;
+      }
+      if (lane == 0) {
+        pub[0] = beta;
+        pub[1] = rr0;
+        pub[2] = stop ? 1.0 : 0.0;
+      }
+    }
+    cl.sync();                                // Householder vector published
+    const double* opub = cl.map_shared_rank(pub, owner);
+    const double beta = opub[0];
+    if (k == 0) r0 = opub[1];
+    if (opub[2] != 0.0) { rank = k; break; }
+    for (int r = k + tid; r < rp; r += NT) v[r] = opub[4 + r];
+    if (tid == 0) piv[k] = p;
+    __syncthreads();
+    // 3. reflect the unselected columns, downdate their norms
+    for (int c = quad; c < W; c += NQ) {
+      const bool act = stc[c] == -1;
+      double* col = M + (size_t)c * ldm;
+      double w = 0.0;
+      if (act)
+        for (int r = k + ql; r < rp; r += 4) w = fma(v[r], col[r], w);
+      w += __shfl_xor_sync(kFullMask, w, 1);
+      w += __shfl_xor_sync(kFullMask, w, 2);
+      double rk = 0.0;
+      if (act) {
+        w *= beta;
+        for (int r = k + ql; r < rp; r += 4) {
+          const double x = fma(-w, v[r], col[r]);
+          col[r] = x;
+          if (r == k) rk = x;
+        }
+      }
+      rk = __shfl_sync(kFullMask, rk, (tid & 31) & ~3);   // R(k, c), held by the quad's lane 0
+      const double sd = nrm[c] - rk * rk;
+      const bool redo = act && !(sd > 0x1p-26 * nref[c]);
+      double s = 0.0;
+      if (redo)                               // each lane rereads only the rows it wrote
+        for (int r = k + ql; r < rp; r += 4)
+          if (r > k) s = fma(col[r], col[r], s);
+      s += __shfl_xor_sync(kFullMask, s, 1);
+      s += __shfl_xor_sync(kFullMask, s, 2);
+      if (act && ql == 0) {
+        nrm[c] = redo ? s : sd;
+        if (redo) nref[c] = s;
+      }
+    }
+    __syncthreads();
+  }
+  // R11 (rank x rank, row-major) to global scratch: R11(i, j) = M(i, piv[j])
+  double* R11 = Jb.scratch;
+  for (int e = tid; e < W * rank; e += NT) {
+    const int c = e % W, i = e / W, j = stc[c];
+    if (j >= 0) R11[(int64_t)i * rank + j] = M[(size_t)c * ldm + i];
+  }
+  if (crank == 0) {
+    if (tid == 0) *Jb.rank_out = rank;
+    for (int t = tid; t < rank; t += NT) Jb.skel_local[t] = piv[t];
+  }
+  cl.sync();                                  // R11 visible to the cluster; no shared reads after
+  // T(:, c) = R11^-1 M(0:rank, c) for the other columns, in place
+  for (int c = quad; c < W; c += NQ) {
+    const bool act = stc[c] == -1;
+    double* col = M + (size_t)c * ldm;
+    for (int r = rank - 1; r >= 0; --r) {
+      double s = 0.0;
+      if (act)
+        for (int q = r + 1 + ql; q < rank; q += 4) s = fma(R11[(int64_t)r * rank + q], col[q], s);
+      s += __shfl_xor_sync(kFullMask, s, 1);
+      s += __shfl_xor_sync(kFullMask, s, 2);
+      if (act && ql == 0) col[r] = (col[r] - s) / R11[(int64_t)r * rank + r];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // rows g0 .. g0 + W - 1 of U (rows x rank, column-major, ld rows_max)
+  for (int e = tid; e < W * rank; e += NT) {
+    const int c = e % W, t = e / W, g = g0 + c;
+    if (g >= rows) continue;
+    const int j = stc[c];
+    Jb.U[(int64_t)t * Jb.rows_max + g] = j >= 0 ? (j == t ? 1.0 : 0.0) : M[(size_t)c * ldm + t];
+  }
+}
+
+// Whether k_hss_id_cl can run with `smem` bytes of shared memory per CTA: at most
+// kIdClMaxSmem, and at least one cluster resident on the device.
+constexpr size_t kIdClMaxSmem = 200u << 10;
+bool id_cl_usable(size_t smem) {
+  if (smem > kIdClMaxSmem) return false;
+  if (cudaFuncSetAttribute(k_hss_id_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kIdCluster);
+  cfg.blockDim = dim3(kIdThreads);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_hss_id_cl, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
 // ------------------------------------------------------------------ parent steps
 // B_{c1} = Qhat(I_c1, J_c2), B_{c2} = Qhat(I_c2, J_c1), and (unless root)
 //   Phi_p   = [Phi_c1(Iloc_c1) - B_c1 Yhat_c2 ; Phi_c2(Iloc_c2) - B_c2 Yhat_c1]
@@ -366,50 +505,13 @@ __global__ __launch_bounds__(256) void k_hss_parent(const HssNodeDev* __restrict
   for (int r = tid; r < kv1 + kv2; r += NT) P.Jcand[r] = r < kv1 ? A.J[r] : Bn.J[r - kv1];
 }
 
-// After a node's IDs: global skeleton indices, and Yhat, Zhat.
-//   leaf:   I = lo + Iloc,  Yhat = V^T Omega1(t),       Zhat = U^T Omega2(t)
-//   parent: I = Icand(Iloc), Yhat = V^T [Yhat_1; Yhat_2], Zhat = U^T [Zhat_1; Zhat_2]
-__global__ __launch_bounds__(256) void k_hss_hat(const HssNodeDev* __restrict__ nodes,
-                                                 const int* __restrict__ list, int rp,
-                                                 const double* __restrict__ om1,
-                                                 const double* __restrict__ om2, int64_t K) {
+// After a node's IDs: its global skeleton indices (a leaf's rows start at lo, a
+// parent's are the candidates its children passed up).
+__global__ void k_hss_skel(const HssNodeDev* __restrict__ nodes, const int* __restrict__ list) {
   const HssNodeDev N = nodes[list[blockIdx.x]];
-  const int tid = threadIdx.x, NT = blockDim.x;
   const int ku = *N.kU, kv = *N.kV;
-  const int ru = N.leaf ? N.hi - N.lo : *N.rows_u;
-  const int rv = N.leaf ? N.hi - N.lo : *N.rows_v;
-  for (int t = tid; t < ku; t += NT) N.I[t] = N.leaf ? N.lo + N.Iloc[t] : N.Icand[N.Iloc[t]];
-  for (int t = tid; t < kv; t += NT) N.J[t] = N.leaf ? N.lo + N.Jloc[t] : N.Jcand[N.Jloc[t]];
-  int k1u = 0, k1v = 0;
-  const double *y1 = nullptr, *y2 = nullptr, *z1 = nullptr, *z2 = nullptr;
-  if (!N.leaf) {
-    const HssNodeDev A = nodes[N.c1], Bn = nodes[N.c2];
-    k1v = *A.kV;
-    k1u = *A.kU;
-    y1 = A.Yh; y2 = Bn.Yh; z1 = A.Zh; z2 = Bn.Zh;
-  }
-  for (int e = tid; e < kv * rp; e += NT) {       // Yhat = V^T (stack), kv x rp
-    const int r = e % kv, c = e / kv;
-    double s = 0.0;
-    for (int t = 0; t < rv; ++t) {
-      double x;
-      if (N.leaf) x = om1[(int64_t)c * K + N.lo + t];
-      else x = t < k1v ? y1[(int64_t)c * rp + t] : y2[(int64_t)c * rp + (t - k1v)];
-      s += N.V[(int64_t)r * N.ldU + t] * x;
-    }
-    N.Yh[(int64_t)c * rp + r] = s;
-  }
-  for (int e = tid; e < ku * rp; e += NT) {       // Zhat = U^T (stack), ku x rp
-    const int r = e % ku, c = e / ku;
-    double s = 0.0;
-    for (int t = 0; t < ru; ++t) {
-      double x;
-      if (N.leaf) x = om2[(int64_t)c * K + N.lo + t];
-      else x = t < k1u ? z1[(int64_t)c * rp + t] : z2[(int64_t)c * rp + (t - k1u)];
-      s += N.U[(int64_t)r * N.ldU + t] * x;
-    }
-    N.Zh[(int64_t)c * rp + r] = s;
-  }
+  for (int t = threadIdx.x; t < ku; t += blockDim.x) N.I[t] = N.leaf ? N.lo + N.Iloc[t] : N.Icand[N.Iloc[t]];
+  for (int t = threadIdx.x; t < kv; t += blockDim.x) N.J[t] = N.leaf ? N.lo + N.Jloc[t] : N.Jcand[N.Jloc[t]];
 }
 
 __global__ void k_read_k(const MergeScalars* scal, int64_t mid, int* out) { *out = scal[mid].K; }
@@ -464,6 +566,7 @@ struct HssLayout {
   int* dK;
   double *om1, *om2, *Y, *Z;
   HssCols xc;
+  int32_t* lid;               // leaf of each Qhat index
   std::vector<HNodeHost> tree;
   int root = 0;
   std::vector<HssNodeDev> nd;
@@ -488,6 +591,7 @@ void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts&
   L.xc.col = b.take<const double*>(K);
   L.xc.lo = b.take<int32_t>(K);
   L.xc.hi = b.take<int32_t>(K);
+  L.lid = b.take<int32_t>(K);
   L.tree.clear();
   L.root = build_tree(L.tree, 0, std::max(K, 1), 0, hl);
   const int nn = (int)L.tree.size();
@@ -537,38 +641,7 @@ void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts&
   L.bytes = b.off;
 }
 
-void launch_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, size_t& tab_off, QhatSrc q,
-                  HssCols xc, cudaStream_t st) {
-  if (g.empty()) return;
-  std::vector<int64_t> cum(g.size() + 1, 0);
-  for (size_t i = 0; i < g.size(); ++i) cum[i + 1] = cum[i] + cdiv64(g[i].M, TB) * cdiv64(g[i].N, TB);
-  tab_off = (tab_off + 255) & ~size_t(255);
-  HGemm* dj = reinterpret_cast<HGemm*>(dev_tab + tab_off);
-  tab_off += g.size() * sizeof(HGemm);
-  tab_off = (tab_off + 255) & ~size_t(255);
-  int64_t* dc = reinterpret_cast<int64_t*>(dev_tab + tab_off);
-  tab_off += cum.size() * 8;
-  if (tab_off > kTabBytes) return;
-  cudaMemcpyAsync(dj, g.data(), g.size() * sizeof(HGemm), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(dc, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice, st);
-  if (cum.back() > 0) k_hss_gemm<<<(unsigned)cum.back(), 256, 0, st>>>(dj, (int)g.size(), dc, q, xc);
-}
-
-HGemm gemm0() {
-  HGemm g;
-  std::memset(&g, 0, sizeof(g));
-  g.alpha = 1.0;
-  return g;
-}
-
 }  // namespace
-
-void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, size_t& tab_off,
-                        cudaStream_t st) {
-  QhatSrc q{};
-  HssCols xc{};
-  launch_gemms(g, dev_tab, tab_off, q, xc, st);
-}
 
 // The largest sample an HSS merge may grow to: r + p doubled hss_grow times.
 int hss_rp_max(const tdc_opts& o) { return o.hss_rp << std::max(0, std::min(o.hss_grow, 4)); }
@@ -579,17 +652,39 @@ int hss_rp_max(const tdc_opts& o) { return o.hss_rp << std::max(0, std::min(o.hs
 constexpr int kHssSlices = 7;
 
 // Workspace of the split GEMMs of one HSS merge of order m (K <= m kept columns, rp
-// samples, leaves of at most hss_leaf): the larger of the sampling batch (Qhat Omega1,
-// Qhat^T Omega2) and a leaf batch (X(:, t) D_t or X(:, t) U_t for every leaf t).
+// samples, leaves of at most hss_leaf): the largest of its batches, sized on the tree of
+// K = m (which has the most nodes on every level) with every leaf at the full leaf size:
+// the sampling (Qhat Omega1, Qhat^T Omega2), one level's hats (V^T S, U^T S), one level of
+// the up-sweep (X(:, t) U_t or [G_1 G_2] U_p), one level's couplings (G B and F V^T), the
+// leaves' X(:, t) D_t and their F_t V_t^T.
 static size_t hss_split_bytes(int64_t m, const tdc_opts& o, int rp) {
   const int hl = std::max(o.hss_leaf, 2);
-  std::vector<SgProblem> sampling(2, sg_problem((int)m, rp, (int)m, SgOp{}, SgOp{}, nullptr, 0));
-  std::vector<SgProblem> leaves;
-  for (int64_t lo = 0; lo < m; lo += hl) {
-    const int sz = (int)std::min<int64_t>(hl, m - lo);
-    leaves.push_back(sg_problem((int)m, std::max(sz, rp), sz, SgOp{}, SgOp{}, nullptr, 0));
+  const int mi = (int)m, kin = std::max(hl, 2 * rp);
+  std::vector<HNodeHost> tree;
+  build_tree(tree, 0, std::max(mi, 1), 0, hl);
+  int maxlev = 0, nleaves = 0;
+  for (const HNodeHost& h : tree) {
+    maxlev = std::max(maxlev, h.level);
+    nleaves += h.c1 < 0;
   }
-  return std::max(split_gemm_bytes(sampling, kHssSlices), split_gemm_bytes(leaves, kHssSlices));
+  std::vector<int> nodes(maxlev + 1, 0), parents(maxlev + 1, 0);
+  for (const HNodeHost& h : tree) {
+    nodes[h.level] += 1;
+    parents[h.level] += h.c1 >= 0;
+  }
+  auto batch = [&](int count, int M, int N, int K) {
+    std::vector<SgProblem> v((size_t)std::max(count, 0), sg_problem(M, N, K, SgOp{}, SgOp{}, nullptr, 0));
+    return v.empty() ? size_t(0) : split_gemm_bytes(v, kHssSlices);
+  };
+  size_t b = batch(2, mi, rp, mi);
+  b = std::max(b, batch(nleaves, mi, hl, hl));
+  b = std::max(b, batch(nleaves, mi, hl, rp));
+  for (int l = 0; l <= maxlev; ++l) {
+    b = std::max(b, batch(2 * nodes[l], rp, rp, kin));
+    b = std::max(b, batch(nodes[l], mi, rp, kin));
+    b = std::max(b, batch(2 * parents[l], mi, rp, rp));
+  }
+  return b;
 }
 
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o) {
@@ -660,11 +755,24 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om1, K, rp, seed, 1);
     k_hss_omega<<<grid_cap((int64_t)K * rp / 256 + 1, 8), 256, 0, st>>>(L.om2, K, rp, seed, 2);
     k_hss_cols<<<grid_cap(K / 256 + 1, 4), 256, 0, st>>>(hJ, w, xc);
-    {                                           // on the split-precision tensor-core GEMM
+    // on the split-precision tensor-core GEMM, with Qhat's diagonal leaf blocks read as
+    // zero: Y and Z are then the leaves' Phi = Y(t) - D_t Omega1(t) and
+    // Theta = Z(t) - D_t^T Omega2(t) without the subtraction
+    maxlev = 0;
+    for (int i = 0; i < nn; ++i) maxlev = std::max(maxlev, tree[i].level);
+    byl.assign(maxlev + 1, {});
+    for (int i = 0; i < nn; ++i) byl[tree[i].level].push_back(i);
+    {
+      std::vector<int32_t> lid(K);
+      for (int i = 0; i < nn; ++i)
+        if (nd[i].leaf)
+          for (int j = tree[i].lo; j < tree[i].hi; ++j) lid[j] = i;
+      cudaMemcpyAsync(L.lid, lid.data(), (size_t)K * 4, cudaMemcpyHostToDevice, st);
       SgOp qa;
       qa.mode = SG_QHAT;
       qa.wcol = q.wcol;
       qa.sinv = q.sinv;
+      qa.lid = nn > 1 ? L.lid : nullptr;
       SgOp qt = qa;
       qt.mode = SG_QHAT_T;
       std::vector<SgProblem> g{sg_problem(K, rp, K, qa, sg_dense(L.om1, K), L.Y, K),
@@ -672,34 +780,12 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       const int rc = split_gemm(g, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
       if (rc) return rc == 3 ? 3 : 4;
     }
-    // ---- leaves: Phi = Y(t) - D Omega1(t), Theta = Z(t) - D^T Omega2(t), in place
-    maxlev = 0;
-    for (int i = 0; i < nn; ++i) maxlev = std::max(maxlev, tree[i].level);
-    byl.assign(maxlev + 1, {});
-    for (int i = 0; i < nn; ++i) byl[tree[i].level].push_back(i);
-    if (nn > 1) {
-      std::vector<HGemm> g;
-      for (int i = 0; i < nn; ++i) {
-        if (!nd[i].leaf) continue;
-        const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
-        HGemm a = gemm0();
-        a.M = sz; a.N = rp; a.K = sz;
-        a.a.mode = HOP_QHAT; a.a.r0 = lo; a.a.c0 = lo;
-        a.b.mode = HOP_DENSE; a.b.p = L.om1; a.b.ld = K; a.b.r0 = lo;
-        a.C = L.Y + lo; a.ldc = K; a.alpha = -1.0; a.beta = 1.0;
-        g.push_back(a);
-        HGemm b = a;
-        b.a.mode = HOP_QHAT_T;
-        b.b.p = L.om2;
-        b.C = L.Z + lo;
-        g.push_back(b);
-      }
-      launch_gemms(g, tab, toff, q, xc, st);
-    }
-    phase_mark(10, false, 5, st);
+    phase_mark(10, false, 6, st);
     phase_mark(11, true, 0, st);
     // ---- interpolative decompositions, leaves to root
     const size_t id_smem = (size_t)(rmax + rp) * 8 + (size_t)rmax * 4 + 64;
+    const IdClShape ish = id_cl_shape(rmax, rp);
+    const bool id_cl = id_cl_usable(ish.smem);
     int* lp = L.lists;
     for (int lev = maxlev; lev >= 1; --lev) {
       std::vector<int> parents, all;
@@ -740,10 +826,44 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       HIdJob* did = reinterpret_cast<HIdJob*>(tab + toff);
       cudaMemcpyAsync(did, ids.data(), ids.size() * sizeof(HIdJob), cudaMemcpyHostToDevice, st);
       toff += ids.size() * sizeof(HIdJob);
-      k_hss_id<<<(unsigned)ids.size(), 256, id_smem, st>>>(did, o.hss_tol, rp);
+      if (id_cl)
+        k_hss_id_cl<<<(unsigned)ids.size() * kIdCluster, kIdThreads, ish.smem, st>>>(did, o.hss_tol, rp, ish.W,
+                                                                                     ish.ldm);
+      else
+        k_hss_id<<<(unsigned)ids.size(), 256, id_smem, st>>>(did, o.hss_tol, rp);
       cudaMemcpyAsync(lp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st);
-      k_hss_hat<<<(unsigned)all.size(), 256, 0, st>>>(L.dnodes, lp, rp, L.om1, L.om2, K);
+      k_hss_skel<<<(unsigned)all.size(), 128, 0, st>>>(L.dnodes, lp);
       lp += all.size();
+      // Yhat = V^T S1, Zhat = U^T S2 with S = the node's rows of Omega (leaf) or its
+      // children's stacked Yhat / Zhat (parent)
+      std::vector<SgProblem> hg;
+      for (int i : all) {
+        SgProblem y = sg_problem(rp, rp, 0, sg_dense(nd[i].V, nd[i].ldU, true), SgOp{}, nd[i].Yh, rp);
+        y.Mdev = nd[i].kV;
+        SgProblem z = y;
+        z.a.p = nd[i].U;
+        z.C = nd[i].Zh;
+        z.Mdev = nd[i].kU;
+        if (nd[i].leaf) {
+          y.K = z.K = tree[i].hi - tree[i].lo;
+          y.b = sg_dense(L.om1, K);
+          z.b = sg_dense(L.om2, K);
+          y.b.r0 = z.b.r0 = tree[i].lo;
+        } else {
+          const int c1 = tree[i].c1, c2 = tree[i].c2;
+          y.K = z.K = 2 * rp;
+          y.Kdev = nd[i].rows_v;
+          z.Kdev = nd[i].rows_u;
+          y.b.mode = z.b.mode = SG_STACK_ROWS;
+          y.b.p = nd[c1].Yh; y.b.p2 = nd[c2].Yh; y.b.split = nd[c1].kV;
+          z.b.p = nd[c1].Zh; z.b.p2 = nd[c2].Zh; z.b.split = nd[c1].kU;
+          y.b.ld = y.b.ld2 = z.b.ld = z.b.ld2 = rp;
+        }
+        hg.push_back(y);
+        hg.push_back(z);
+      }
+      const int rc = split_gemm(hg, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
+      if (rc) return rc == 3 ? 3 : 4;
     }
     const int root = L.root;
     if (!nd[root].leaf) {                       // root: couplings of its children only
@@ -753,7 +873,7 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     }
     if (nn > 1) k_hss_saturated_zero(L.dK, st);
     if (nn > 1) k_hss_saturated<<<1, 256, 0, st>>>(L.dnodes, nn, rp, L.dK);
-    phase_mark(11, false, 3 * maxlev + 2, st);
+    phase_mark(11, false, 7 * maxlev + 2, st);
     if (nn > 1) {                               // ranks that reached the sample count
       int sat = 0;
       cudaMemcpyAsync(&sat, L.dK, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -776,69 +896,70 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   auto& nd = L.nd;
   phase_mark(12, true, 0, st);
 
-  // ---- multiply: Out = X Qhat_hss, X = Q_sel (m rows, K kept columns)
+  // ---- multiply: Out = X Qhat_hss, X = Q_sel (m rows, K kept columns), every product
+  // on the split-precision tensor-core GEMM
+  int nmul = 0;
+  auto run_split = [&](std::vector<SgProblem>& g) -> int {
+    if (g.empty()) return 0;
+    nmul += 3;
+    const int rc = split_gemm(g, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
+    return rc == 0 ? 0 : (rc == 3 ? 3 : 4);
+  };
   SgOp xo;                                  // gathered columns of Q_sel (kept order)
   xo.mode = SG_XCOLS;
   xo.xcol = xc.col;
   xo.xlo = xc.lo;
   xo.xhi = xc.hi;
   for (int lev = maxlev; lev >= 1; --lev) {   // up-sweep: G = X(:, t) U, G_p = [G_1 G_2] U_p
-    std::vector<HGemm> g;
-    std::vector<SgProblem> gl;                // leaves: on the split-precision GEMM
+    std::vector<SgProblem> g;
     for (int i : byl[lev]) {
+      SgProblem p;
       if (nd[i].leaf) {
         SgOp xa = xo;
         xa.c0 = tree[i].lo;
-        SgProblem p = sg_problem(m, rp, tree[i].hi - tree[i].lo, xa, sg_dense(nd[i].U, rmax), nd[i].G, m);
-        p.Ndev = nd[i].kU;
-        gl.push_back(p);
-        continue;
+        p = sg_problem(m, rp, tree[i].hi - tree[i].lo, xa, sg_dense(nd[i].U, rmax), nd[i].G, m);
+      } else {
+        SgOp a;
+        a.mode = SG_STACK;
+        a.p = nd[tree[i].c1].G;
+        a.p2 = nd[tree[i].c2].G;
+        a.ld = a.ld2 = m;
+        a.split = nd[tree[i].c1].kU;
+        p = sg_problem(m, rp, 2 * rp, a, sg_dense(nd[i].U, rmax), nd[i].G, m);
+        p.Kdev = nd[i].rows_u;
       }
-      HGemm a = gemm0();
-      a.M = m; a.N = rp; a.Ndev = nd[i].kU;
-      a.C = nd[i].G; a.ldc = m;
-      a.b.mode = HOP_DENSE; a.b.p = nd[i].U; a.b.ld = rmax;
-      a.K = 2 * rp; a.Kdev = nd[i].rows_u;
-      a.a.mode = HOP_STACK; a.a.p = nd[tree[i].c1].G; a.a.ld = m;
-      a.a.p2 = nd[tree[i].c2].G; a.a.ld2 = m; a.a.split = nd[tree[i].c1].kU;
-      g.push_back(a);
+      p.Ndev = nd[i].kU;
+      g.push_back(p);
     }
-    if (!gl.empty()) {
-      const int rc = split_gemm(gl, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
-      if (rc) return rc == 3 ? 3 : 4;
-    }
-    launch_gemms(g, tab, toff, q, xc, st);
+    if (const int rc = run_split(g)) return rc;
   }
   for (int lev = 0; lev < maxlev; ++lev) {     // couplings and down-sweep, root to leaves
-    std::vector<HGemm> g1, g2;
+    std::vector<SgProblem> g1, g2;
     for (int p : byl[lev]) {
       if (nd[p].leaf) continue;
       const int c1 = tree[p].c1, c2 = tree[p].c2;
       for (int side = 0; side < 2; ++side) {
         const int dst = side ? c2 : c1, src = side ? c1 : c2;
-        HGemm a = gemm0();                     // F_dst = G_src B_src
-        a.M = m; a.N = rp; a.Ndev = nd[dst].kV; a.K = rp; a.Kdev = nd[src].kU;
-        a.a.mode = HOP_DENSE; a.a.p = nd[src].G; a.a.ld = m;
-        a.b.mode = HOP_DENSE; a.b.p = nd[src].B; a.b.ld = rp;
-        a.C = nd[dst].F; a.ldc = m;
+        // F_dst = G_src B_src
+        SgProblem a = sg_problem(m, rp, rp, sg_dense(nd[src].G, m), sg_dense(nd[src].B, rp), nd[dst].F, m);
+        a.Ndev = nd[dst].kV;
+        a.Kdev = nd[src].kU;
         g1.push_back(a);
         if (!nd[p].root) {                     // F_dst += F_p V_p(rows of dst)^T
-          HGemm b = gemm0();
-          b.M = m; b.N = rp; b.Ndev = nd[dst].kV; b.K = rp; b.Kdev = nd[p].kV;
-          b.a.mode = HOP_DENSE; b.a.p = nd[p].F; b.a.ld = m;
-          b.b.mode = HOP_DENSE_T; b.b.p = nd[p].V; b.b.ld = rmax;
-          b.b.row_off_dev = side ? nd[c1].kV : nullptr;
-          b.C = nd[dst].F; b.ldc = m; b.beta = 1.0;
+          SgProblem b = sg_problem(m, rp, rp, sg_dense(nd[p].F, m), sg_dense(nd[p].V, rmax, true), nd[dst].F, m);
+          b.b.off_dev = side ? nd[c1].kV : nullptr;
+          b.Ndev = nd[dst].kV;
+          b.Kdev = nd[p].kV;
+          b.beta = 1.0;
           g2.push_back(b);
         }
       }
     }
-    launch_gemms(g1, tab, toff, q, xc, st);
-    launch_gemms(g2, tab, toff, q, xc, st);
+    if (const int rc = run_split(g1)) return rc;
+    if (const int rc = run_split(g2)) return rc;
   }
-  {                                             // leaves: Out(:, pos(t)) = X(:, t) D + F V^T
-    std::vector<HGemm> g2;
-    std::vector<SgProblem> g1;                  // X(:, t) D_t on the split-precision GEMM
+  {                                             // leaves: Out(:, pos(t)) = X(:, t) D_t + F_t V_t^T
+    std::vector<SgProblem> g1, g2;
     for (int i = 0; i < nn; ++i) {
       if (!nd[i].leaf) continue;
       const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
@@ -855,20 +976,18 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       p.cc0 = lo;
       g1.push_back(p);
       if (nn > 1) {
-        HGemm b = gemm0();
-        b.M = m; b.N = sz; b.K = rp; b.Kdev = nd[i].kV;
-        b.a.mode = HOP_DENSE; b.a.p = nd[i].F; b.a.ld = m;
-        b.b.mode = HOP_DENSE_T; b.b.p = nd[i].V; b.b.ld = rmax;
-        b.cmode = HC_PTRS; b.cptrs = outp; b.cc0 = lo;
+        SgProblem b = sg_problem(m, sz, rp, sg_dense(nd[i].F, m), sg_dense(nd[i].V, rmax, true), nullptr, 0);
+        b.Kdev = nd[i].kV;
+        b.cptrs = outp;
+        b.cc0 = lo;
         b.beta = 1.0;
         g2.push_back(b);
       }
     }
-    const int rc = split_gemm(g1, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
-    if (rc) return rc == 3 ? 3 : 4;
-    launch_gemms(g2, tab, toff, q, xc, st);
+    if (const int rc = run_split(g1)) return rc;
+    if (const int rc = run_split(g2)) return rc;
   }
-  phase_mark(12, false, 4 * maxlev + 2, st);
+  phase_mark(12, false, nmul, st);
   return toff > kTabBytes ? 3 : 0;
 }
 

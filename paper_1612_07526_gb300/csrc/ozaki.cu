@@ -842,7 +842,8 @@ struct SgJob {                       // CUtensorMap members force 64-byte alignm
   SgOp a, b;                         // A (M x K) and B (K x N), element by element
   double* C;                         // C[r, c] = C[r + c ldc], or cptrs[cc0 + c][r]
   double* const* cptrs;
-  const int* Ndev;                   // actual column count (device), or null
+  const int *Mdev, *Ndev, *Kdev;     // actual sizes (device), or null
+  double alpha, beta;
   uint16_t *as, *bs;
   int32_t *aexp, *bexp;              // INT32_MIN: a zero row / column
   int64_t ldc;
@@ -855,15 +856,36 @@ __device__ __forceinline__ double sg_at(const SgOp& o, int row, int col) {
   switch (o.mode) {
     case SG_DENSE: return o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld];
     case SG_DENSE_T: return o.p[(int64_t)(o.c0 + col) + (int64_t)(o.r0 + row) * o.ld];
-    case SG_QHAT: return o.wcol[o.c0 + col][o.r0 + row] * o.sinv[o.c0 + col];
-    case SG_QHAT_T: return o.wcol[o.r0 + row][o.c0 + col] * o.sinv[o.r0 + row];
+    case SG_QHAT: {
+      const int j = o.r0 + row, i = o.c0 + col;
+      return o.lid && o.lid[j] == o.lid[i] ? 0.0 : o.wcol[i][j] * o.sinv[i];
+    }
+    case SG_QHAT_T: {
+      const int i = o.r0 + row, j = o.c0 + col;
+      return o.lid && o.lid[j] == o.lid[i] ? 0.0 : o.wcol[i][j] * o.sinv[i];
+    }
     case SG_XCOLS: {
       const int j = o.c0 + col;
       return row >= o.xlo[j] && row < o.xhi[j] ? o.xcol[j][row] : 0.0;
     }
+    case SG_STACK:
+      return col < o.k1 ? o.p[(int64_t)(o.r0 + row) + (int64_t)col * o.ld]
+                        : o.p2[(int64_t)(o.r0 + row) + (int64_t)(col - o.k1) * o.ld2];
+    case SG_STACK_ROWS:
+      return row < o.k1 ? o.p[(int64_t)row + (int64_t)(o.c0 + col) * o.ld]
+                        : o.p2[(int64_t)(row - o.k1) + (int64_t)(o.c0 + col) * o.ld2];
     default: return 0.0;
   }
 }
+// The operand with its device-held offsets read once: k1 of the stacked forms, the
+// column offset of SG_DENSE_T.
+__device__ __forceinline__ SgOp sg_resolve(const SgOp& o) {
+  SgOp r = o;
+  if (o.split) r.k1 = *o.split;
+  if (o.off_dev) r.c0 += *o.off_dev;
+  return r;
+}
+__device__ __forceinline__ int sg_size(const int* dev, int host) { return dev ? min(*dev, host) : host; }
 // whether consecutive rows of the operand are adjacent in memory (else consecutive columns)
 __device__ __forceinline__ bool sg_rows_contiguous(int mode) { return mode != SG_DENSE_T && mode != SG_QHAT_T; }
 
@@ -879,10 +901,11 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   const SgJob& J = jobs[jb];
   const int r0 = (int)(blockIdx.x - cum[jb]) * 32;
   const int tid = threadIdx.x;
-  const int M = J.M, K = J.K;
+  const int M = J.M, K = sg_size(J.Kdev, J.K), Me = sg_size(J.Mdev, J.M);
+  const SgOp A = sg_resolve(J.a);
   auto at = [&](int r, int k) -> double {          // A[r0 + r, k], zero outside
-    if (r0 + r >= M || k >= K) return 0.0;
-    return sg_at(J.a, r0 + r, k);
+    if (r0 + r >= Me || k >= K) return 0.0;
+    return sg_at(A, r0 + r, k);
   };
   const bool rowc = sg_rows_contiguous(J.a.mode);
   // pass 1: row maxima on the magnitude bits
@@ -974,9 +997,11 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
   const int c = (int)(blockIdx.x - cum[jb]) * 8 + (int)(threadIdx.x >> 5);
   if (c >= J.N) return;                             // uniform over the warp
   const bool live = !J.Ndev || c < *J.Ndev;         // columns past the actual count are zero
-  auto at = [&](int k) -> double { return live && k < J.K ? sg_at(J.b, k, c) : 0.0; };
+  const int K = sg_size(J.Kdev, J.K);
+  const SgOp B = sg_resolve(J.b);
+  auto at = [&](int k) -> double { return live && k < K ? sg_at(B, k, c) : 0.0; };
   unsigned long long m = 0ull;
-  for (int k = lane; k < J.K; k += 32) {
+  for (int k = lane; k < K; k += 32) {
     const unsigned long long v = (unsigned long long)__double_as_longlong(at(k)) & 0x7FFFFFFFFFFFFFFFull;
     m = v > m ? v : m;
   }
@@ -1245,17 +1270,19 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
       }
       if (!ok) break;
       const int grow = T.row0 + row;
-      const int ncol = J.Ndev ? min(*J.Ndev, J.N) : J.N;
-      if (grow < J.M) {
+      const int ncol = sg_size(J.Ndev, J.N);
+      if (grow < sg_size(J.Mdev, J.M)) {
         const int ea = J.aexp[grow];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = T.ct * kOzBN + half * 32 + j;
           if (col < ncol) {
             const int eb = J.bexp[col];
-            const double x = (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
-            if (J.cptrs) J.cptrs[J.cc0 + col][grow] = x;
-            else J.C[(int64_t)grow + (int64_t)col * J.ldc] = x;
+            double x = (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
+            double* dst = J.cptrs ? J.cptrs[J.cc0 + col] + grow : J.C + (int64_t)grow + (int64_t)col * J.ldc;
+            x *= J.alpha;
+            if (J.beta != 0.0) x = fma(J.beta, *dst, x);
+            *dst = x;
           }
         }
       }
@@ -1385,7 +1412,11 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
     J.ldc = p.ldc;
     J.cptrs = p.cptrs;
     J.cc0 = p.cc0;
+    J.Mdev = p.Mdev;
     J.Ndev = p.Ndev;
+    J.Kdev = p.Kdev;
+    J.alpha = p.alpha;
+    J.beta = p.beta;
     J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
     J.bs = reinterpret_cast<uint16_t*>(take((size_t)S * p.N * J.Kp * 2));
     J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));

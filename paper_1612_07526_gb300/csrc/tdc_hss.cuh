@@ -8,39 +8,6 @@
 
 namespace tdc {
 
-enum : int { HOP_DENSE = 0, HOP_DENSE_T = 1, HOP_QHAT = 2, HOP_QHAT_T = 3, HOP_XCOLS = 4, HOP_STACK = 5,
-             HOP_STACK_ROWS = 6 };
-enum : int { HC_DENSE = 0, HC_SCATTER = 1, HC_PTRS = 2 };
-
-// One operand of a batched GEMM, as a logical matrix element (r, c).
-struct HOp {
-  int mode;
-  int r0, c0;                 // offsets (global Qhat indices for the generated modes)
-  const double* p;
-  int64_t ld;
-  const double* p2;           // second block (stacked modes)
-  int64_t ld2;
-  const int* split;           // device: size of the first block (stacked modes)
-  const int* ridx;            // optional index maps (generated modes)
-  const int* cidx;
-  const int* row_off_dev;     // device offset added to c0 (transposed dense mode)
-};
-
-struct HGemm {
-  int M, N, K;                // launch-time maxima
-  const int* Mdev;            // device-side actual sizes (optional)
-  const int* Ndev;
-  const int* Kdev;
-  HOp a, b;
-  int cmode;
-  double* C;
-  int64_t ldc;
-  const int32_t* cpos;        // scatter: output column of logical column c is cpos[cc0 + c]
-  double* const* cptrs;       // pointers: output column of logical column c is cptrs[cc0 + c]
-  int cc0;
-  double alpha, beta;
-};
-
 struct HssCols {
   const double** col;         // kept-order columns of Q_sel, at the merge's row 0
   int32_t *lo, *hi;           // rows [lo, hi) where each can be nonzero
@@ -74,9 +41,6 @@ struct HssNodeDev {
 };
 
 size_t hss_arena_bytes(int64_t m, const tdc_opts& o);
-// Batched FP64 GEMMs with dense operands only (job tables staged at dev_tab + tab_off).
-void launch_dense_gemms(const std::vector<HGemm>& g, unsigned char* dev_tab, size_t& tab_off,
-                        cudaStream_t st);
 // Runs Algorithm 1 and the HSS multiply for one merge whose deflation, roots,
 // zhat and norms are in w; writes the K non-deflated output columns.  Reads K on the
 // host (one stream synchronization).  Returns 0, 3 (arena too small) or 4.

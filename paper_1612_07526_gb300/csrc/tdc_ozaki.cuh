@@ -66,21 +66,33 @@ int oz_slice_pairs(int slices);
 //   SG_QHAT_T    wcol[r0 + row][c0 + col] sinv[r0 + row]  (its transpose)
 //   SG_XCOLS     xcol[c0 + col][row] for xlo[c0 + col] <= row < xhi[c0 + col], else 0
 //                (gathered eigenvector columns with their nonzero row ranges)
-// B is read as (k, column); its forms are SG_DENSE, SG_QHAT and SG_XCOLS.  C (M x N) is
-// overwritten, column-major with ldc, or through column pointers cptrs[cc0 + col][row].
-// Ndev (optional, device) holds the actual column count (<= N): B's further columns count
-// as zero and C's are not written.  One call runs a batch: slicing of every A and B, then
-// one persistent GEMM over all their tiles.  The workspace holds the slices (about
+//   SG_STACK     [P P2]: p[(r0 + row) + col ld] for col < k1, else p2[(r0 + row) + (col - k1) ld2]
+//   SG_STACK_ROWS [P; P2]: p[row + (c0 + col) ld] for row < k1, else p2[(row - k1) + (c0 + col) ld2]
+// with k1 = *split (device).  In SG_DENSE_T, off_dev (optional, device) adds to c0.  In
+// the SG_QHAT forms, lid (optional) gives a block index per Qhat index, and entries whose
+// row and column share a block read as zero (Qhat without its diagonal blocks).
+// C = alpha A B + beta C, column-major with ldc, or through column pointers
+// cptrs[cc0 + col][row].  Mdev, Ndev and Kdev (optional, device) hold the actual sizes
+// (<= M, N, K): A's and B's entries past them count as zero, and C's rows and columns past
+// them are not written.  One call runs a batch: slicing of every A and B, then one
+// persistent GEMM over all their tiles.  The workspace holds the slices (about
 // 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives its size.
 // Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
-enum : int { SG_DENSE = 0, SG_DENSE_T = 1, SG_QHAT = 2, SG_QHAT_T = 3, SG_XCOLS = 4 };
+enum : int { SG_DENSE = 0, SG_DENSE_T = 1, SG_QHAT = 2, SG_QHAT_T = 3, SG_XCOLS = 4, SG_STACK = 5,
+             SG_STACK_ROWS = 6 };
 struct SgOp {
   int mode = SG_DENSE;
   int r0 = 0, c0 = 0;
+  int k1 = 0;                       // resolved from split on the device
   const double* p = nullptr;
   int64_t ld = 0;
+  const double* p2 = nullptr;
+  int64_t ld2 = 0;
+  const int* split = nullptr;
+  const int* off_dev = nullptr;
   double* const* wcol = nullptr;
   const double* sinv = nullptr;
+  const int32_t* lid = nullptr;
   const double* const* xcol = nullptr;
   const int32_t* xlo = nullptr;
   const int32_t* xhi = nullptr;
@@ -92,7 +104,10 @@ struct SgProblem {
   int64_t ldc = 0;
   double* const* cptrs = nullptr;
   int cc0 = 0;
+  const int* Mdev = nullptr;
   const int* Ndev = nullptr;
+  const int* Kdev = nullptr;
+  double alpha = 1.0, beta = 0.0;
 };
 inline SgOp sg_dense(const double* p, int64_t ld, bool trans = false) {
   SgOp o;
