@@ -9,7 +9,8 @@
 //                 cluster of 8 CTAs per decomposition with Phi^T held in their
 //                 shared memory; k_hss_id, one CTA and global scratch, where it
 //                 does not fit
-//   k_hss_parent  per parent: sibling couplings B and the parent's Phi, Theta
+//   k_hss_couple  per parent: sibling couplings B (Qhat at the skeletons)
+//   k_hss_parent  per parent: its Phi and Theta from the children's
 //   k_hss_skel    global skeleton indices
 // Every product runs on the split-precision tensor-core GEMM (tdc_ozaki.cuh, 7 slices):
 // the sampling Y = Qhat Omega1 and Z = Qhat^T Omega2 with Qhat's diagonal leaf blocks
@@ -453,24 +454,42 @@ bool id_cl_usable(size_t smem) {
 // B_{c1} = Qhat(I_c1, J_c2), B_{c2} = Qhat(I_c2, J_c1), and (unless root)
 //   Phi_p   = [Phi_c1(Iloc_c1) - B_c1 Yhat_c2 ; Phi_c2(Iloc_c2) - B_c2 Yhat_c1]
 //   Theta_p = [Theta_c1(Jloc_c1) - B_c2^T Zhat_c2 ; Theta_c2(Jloc_c2) - B_c1^T Zhat_c1]
-__global__ __launch_bounds__(256) void k_hss_parent(const HssNodeDev* __restrict__ nodes,
+// in two kernels (the second reads the first's B), each with kParentParts CTAs per
+// parent (blockIdx.y) sharing its elements.
+constexpr int kParentParts = 8;
+__global__ __launch_bounds__(256) void k_hss_couple(const HssNodeDev* __restrict__ nodes,
                                                     const int* __restrict__ plist, int rp, QhatSrc q) {
   const HssNodeDev P = nodes[plist[blockIdx.x]];
   const HssNodeDev A = nodes[P.c1], Bn = nodes[P.c2];
   const int ku1 = *A.kU, kv1 = *A.kV, ku2 = *Bn.kU, kv2 = *Bn.kV;
-  const int tid = threadIdx.x, NT = blockDim.x;
-  for (int e = tid; e < ku1 * kv2; e += NT) {
+  const int t0 = blockIdx.y * blockDim.x + threadIdx.x, NT = gridDim.y * blockDim.x;
+  for (int e = t0; e < ku1 * kv2; e += NT) {
     const int r = e % ku1, c = e / ku1;
     A.B[(int64_t)c * rp + r] = qhat(q, A.I[r], Bn.J[c]);
   }
-  for (int e = tid; e < ku2 * kv1; e += NT) {
+  for (int e = t0; e < ku2 * kv1; e += NT) {
     const int r = e % ku2, c = e / ku2;
     Bn.B[(int64_t)c * rp + r] = qhat(q, Bn.I[r], A.J[c]);
   }
-  __syncthreads();
   if (P.root) return;
+  if (t0 == 0) {
+    *P.rows_u = ku1 + ku2;
+    *P.rows_v = kv1 + kv2;
+  }
+  // skeleton candidates of the parent (global indices), in row order of Phi_p
+  for (int r = t0; r < ku1 + ku2; r += NT) P.Icand[r] = r < ku1 ? A.I[r] : Bn.I[r - ku1];
+  for (int r = t0; r < kv1 + kv2; r += NT) P.Jcand[r] = r < kv1 ? A.J[r] : Bn.J[r - kv1];
+}
+
+__global__ __launch_bounds__(256) void k_hss_parent(const HssNodeDev* __restrict__ nodes,
+                                                    const int* __restrict__ plist, int rp) {
+  const HssNodeDev P = nodes[plist[blockIdx.x]];
+  if (P.root) return;
+  const HssNodeDev A = nodes[P.c1], Bn = nodes[P.c2];
+  const int ku1 = *A.kU, kv1 = *A.kV, ku2 = *Bn.kU, kv2 = *Bn.kV;
+  const int t0 = blockIdx.y * blockDim.x + threadIdx.x, NT = gridDim.y * blockDim.x;
   // Phi_p rows: first ku1 from child 1, then ku2 from child 2
-  for (int e = tid; e < (ku1 + ku2) * rp; e += NT) {
+  for (int e = t0; e < (ku1 + ku2) * rp; e += NT) {
     const int r = e % (ku1 + ku2), c = e / (ku1 + ku2);
     double s;
     if (r < ku1) {
@@ -483,7 +502,7 @@ __global__ __launch_bounds__(256) void k_hss_parent(const HssNodeDev* __restrict
     }
     P.phi[(int64_t)c * P.ldphi + r] = s;
   }
-  for (int e = tid; e < (kv1 + kv2) * rp; e += NT) {
+  for (int e = t0; e < (kv1 + kv2) * rp; e += NT) {
     const int r = e % (kv1 + kv2), c = e / (kv1 + kv2);
     double s;
     if (r < kv1) {
@@ -496,13 +515,6 @@ __global__ __launch_bounds__(256) void k_hss_parent(const HssNodeDev* __restrict
     }
     P.theta[(int64_t)c * P.ldphi + r] = s;
   }
-  if (tid == 0) {
-    *P.rows_u = ku1 + ku2;
-    *P.rows_v = kv1 + kv2;
-  }
-  // skeleton candidates of the parent (global indices), in row order of Phi_p
-  for (int r = tid; r < ku1 + ku2; r += NT) P.Icand[r] = r < ku1 ? A.I[r] : Bn.I[r - ku1];
-  for (int r = tid; r < kv1 + kv2; r += NT) P.Jcand[r] = r < kv1 ? A.J[r] : Bn.J[r - kv1];
 }
 
 // After a node's IDs: its global skeleton indices (a leaf's rows start at lo, a
@@ -681,7 +693,7 @@ static size_t hss_split_bytes(int64_t m, const tdc_opts& o, int rp) {
   b = std::max(b, batch(nleaves, mi, hl, rp));
   for (int l = 0; l <= maxlev; ++l) {
     b = std::max(b, batch(2 * nodes[l], rp, rp, kin));
-    b = std::max(b, batch(nodes[l], mi, rp, kin));
+    b = std::max(b, batch(nodes[l], mi, rp, kin) + batch(nodes[l] - parents[l], mi, hl, hl));
     b = std::max(b, batch(2 * parents[l], mi, rp, rp));
   }
   return b;
@@ -795,7 +807,9 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       }
       if (!parents.empty()) {
         cudaMemcpyAsync(lp, parents.data(), parents.size() * 4, cudaMemcpyHostToDevice, st);
-        k_hss_parent<<<(unsigned)parents.size(), 256, 0, st>>>(L.dnodes, lp, rp, q);
+        const dim3 pg((unsigned)parents.size(), kParentParts);
+        k_hss_couple<<<pg, 256, 0, st>>>(L.dnodes, lp, rp, q);
+        k_hss_parent<<<pg, 256, 0, st>>>(L.dnodes, lp, rp);
         lp += parents.size();
       }
       std::vector<HIdJob> ids;
@@ -868,12 +882,12 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     const int root = L.root;
     if (!nd[root].leaf) {                       // root: couplings of its children only
       cudaMemcpyAsync(lp, &root, 4, cudaMemcpyHostToDevice, st);
-      k_hss_parent<<<1, 256, 0, st>>>(L.dnodes, lp, rp, q);
+      k_hss_couple<<<dim3(1, kParentParts), 256, 0, st>>>(L.dnodes, lp, rp, q);
       lp += 1;
     }
     if (nn > 1) k_hss_saturated_zero(L.dK, st);
     if (nn > 1) k_hss_saturated<<<1, 256, 0, st>>>(L.dnodes, nn, rp, L.dK);
-    phase_mark(11, false, 7 * maxlev + 2, st);
+    phase_mark(11, false, 8 * maxlev + 2, st);
     if (nn > 1) {                               // ranks that reached the sample count
       int sat = 0;
       cudaMemcpyAsync(&sat, L.dK, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -910,6 +924,21 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
   xo.xcol = xc.col;
   xo.xlo = xc.lo;
   xo.xhi = xc.hi;
+  // X(:, t) D_t, the leaf's own block of the output (overwritten here; the down-sweep's
+  // F_t V_t^T is added at the end), reusing the slices of X(:, t) of its G = X(:, t) U
+  auto leaf_d = [&](int i, SgOp xa) {
+    SgOp db;
+    db.mode = SG_QHAT;
+    db.r0 = tree[i].lo;
+    db.c0 = tree[i].lo;
+    db.wcol = q.wcol;
+    db.sinv = q.sinv;
+    const int sz = tree[i].hi - tree[i].lo;
+    SgProblem p = sg_problem(m, sz, sz, xa, db, nullptr, 0);
+    p.cptrs = outp;
+    p.cc0 = tree[i].lo;
+    return p;
+  };
   for (int lev = maxlev; lev >= 1; --lev) {   // up-sweep: G = X(:, t) U, G_p = [G_1 G_2] U_p
     std::vector<SgProblem> g;
     for (int i : byl[lev]) {
@@ -918,6 +947,12 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
         SgOp xa = xo;
         xa.c0 = tree[i].lo;
         p = sg_problem(m, rp, tree[i].hi - tree[i].lo, xa, sg_dense(nd[i].U, rmax), nd[i].G, m);
+        p.Ndev = nd[i].kU;
+        g.push_back(p);
+        SgProblem dp = leaf_d(i, xa);
+        dp.a_from = (int)g.size() - 1;
+        g.push_back(dp);
+        continue;
       } else {
         SgOp a;
         a.mode = SG_STACK;
@@ -958,34 +993,25 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     if (const int rc = run_split(g1)) return rc;
     if (const int rc = run_split(g2)) return rc;
   }
-  {                                             // leaves: Out(:, pos(t)) = X(:, t) D_t + F_t V_t^T
-    std::vector<SgProblem> g1, g2;
+  {                                             // leaves: Out(:, pos(t)) += F_t V_t^T
+    std::vector<SgProblem> g;
     for (int i = 0; i < nn; ++i) {
       if (!nd[i].leaf) continue;
       const int lo = tree[i].lo, sz = tree[i].hi - tree[i].lo;
-      SgOp xa = xo;
-      xa.c0 = lo;
-      SgOp db;
-      db.mode = SG_QHAT;
-      db.r0 = lo;
-      db.c0 = lo;
-      db.wcol = q.wcol;
-      db.sinv = q.sinv;
-      SgProblem p = sg_problem(m, sz, sz, xa, db, nullptr, 0);
-      p.cptrs = outp;
-      p.cc0 = lo;
-      g1.push_back(p);
-      if (nn > 1) {
-        SgProblem b = sg_problem(m, sz, rp, sg_dense(nd[i].F, m), sg_dense(nd[i].V, rmax, true), nullptr, 0);
-        b.Kdev = nd[i].kV;
-        b.cptrs = outp;
-        b.cc0 = lo;
-        b.beta = 1.0;
-        g2.push_back(b);
+      if (nn == 1) {                            // a single leaf: Out = X Qhat
+        SgOp xa = xo;
+        xa.c0 = lo;
+        g.push_back(leaf_d(i, xa));
+        continue;
       }
+      SgProblem b = sg_problem(m, sz, rp, sg_dense(nd[i].F, m), sg_dense(nd[i].V, rmax, true), nullptr, 0);
+      b.Kdev = nd[i].kV;
+      b.cptrs = outp;
+      b.cc0 = lo;
+      b.beta = 1.0;
+      g.push_back(b);
     }
-    if (const int rc = run_split(g1)) return rc;
-    if (const int rc = run_split(g2)) return rc;
+    if (const int rc = run_split(g)) return rc;
   }
   phase_mark(12, false, nmul, st);
   return toff > kTabBytes ? 3 : 0;

@@ -274,16 +274,22 @@ __global__ __launch_bounds__(256) void k_oz_slice_a(const MergeJob* __restrict__
   const int tid = threadIdx.x;
   const int r = tid & 31, kq = tid >> 5;
   const bool rvalid = r0 + r < rows_h;
-  // pass 1: row maxima, on the magnitude bits (integer order = order of |x|)
+  // pass 1: row maxima, on the magnitude bits (integer order = order of |x|), four
+  // independent loads in flight per thread
   unsigned long long mx = 0ull;
-  for (int k = kq; k < klen; k += 8) {
-    const int kg = padded_to_grouped(kb + k, c1, c3, K, P1, P3);
-    const int row = rowbase + r0 + r;
-    if (kg >= 0 && rvalid && row >= w.klo[J.v_off + kg] && row < w.khi[J.v_off + kg]) {
-      const unsigned long long v =
-          (unsigned long long)__double_as_longlong(colptr[kg][row]) & 0x7FFFFFFFFFFFFFFFull;
-      mx = v > mx ? v : mx;
+  const int row = rowbase + r0 + r;
+  for (int k0 = kq; k0 < klen; k0 += 32) {
+    unsigned long long v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 8 * u;
+      const int kg = k < klen ? padded_to_grouped(kb + k, c1, c3, K, P1, P3) : -1;
+      v[u] = kg >= 0 && rvalid && row >= w.klo[J.v_off + kg] && row < w.khi[J.v_off + kg]
+                 ? (unsigned long long)__double_as_longlong(colptr[kg][row]) & 0x7FFFFFFFFFFFFFFFull
+                 : 0ull;
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) mx = v[u] > mx ? v[u] : mx;
   }
   s_max[kq][r] = mx;
   __syncthreads();
@@ -851,32 +857,6 @@ struct SgJob {                       // CUtensorMap members force 64-byte alignm
   int32_t cc0, pad_;
 };
 
-// Element (row, col) of an operand in one of the SG_* forms.
-__device__ __forceinline__ double sg_at(const SgOp& o, int row, int col) {
-  switch (o.mode) {
-    case SG_DENSE: return o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld];
-    case SG_DENSE_T: return o.p[(int64_t)(o.c0 + col) + (int64_t)(o.r0 + row) * o.ld];
-    case SG_QHAT: {
-      const int j = o.r0 + row, i = o.c0 + col;
-      return o.lid && o.lid[j] == o.lid[i] ? 0.0 : o.wcol[i][j] * o.sinv[i];
-    }
-    case SG_QHAT_T: {
-      const int i = o.r0 + row, j = o.c0 + col;
-      return o.lid && o.lid[j] == o.lid[i] ? 0.0 : o.wcol[i][j] * o.sinv[i];
-    }
-    case SG_XCOLS: {
-      const int j = o.c0 + col;
-      return row >= o.xlo[j] && row < o.xhi[j] ? o.xcol[j][row] : 0.0;
-    }
-    case SG_STACK:
-      return col < o.k1 ? o.p[(int64_t)(o.r0 + row) + (int64_t)col * o.ld]
-                        : o.p2[(int64_t)(o.r0 + row) + (int64_t)(col - o.k1) * o.ld2];
-    case SG_STACK_ROWS:
-      return row < o.k1 ? o.p[(int64_t)row + (int64_t)(o.c0 + col) * o.ld]
-                        : o.p2[(int64_t)(row - o.k1) + (int64_t)(o.c0 + col) * o.ld2];
-    default: return 0.0;
-  }
-}
 // The operand with its device-held offsets read once: k1 of the stacked forms, the
 // column offset of SG_DENSE_T.
 __device__ __forceinline__ SgOp sg_resolve(const SgOp& o) {
@@ -886,12 +866,43 @@ __device__ __forceinline__ SgOp sg_resolve(const SgOp& o) {
   return r;
 }
 __device__ __forceinline__ int sg_size(const int* dev, int host) { return dev ? min(*dev, host) : host; }
-// whether consecutive rows of the operand are adjacent in memory (else consecutive columns)
-__device__ __forceinline__ bool sg_rows_contiguous(int mode) { return mode != SG_DENSE_T && mode != SG_QHAT_T; }
+// Element (row, col) of an operand in the SG_* form MODE (the forms are listed with
+// SgOp), without branches: an element outside the
+// operand (ok false) is read at the operand's first element and replaced by zero, so that
+// the loads of several elements can be in flight together.
+template <int MODE>
+__device__ __forceinline__ double sg_ld(const SgOp& o, int row, int col, bool ok) {
+  row = ok ? row : 0;
+  col = ok ? col : 0;
+  double x;
+  if constexpr (MODE == SG_DENSE) {
+    x = o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld];
+  } else if constexpr (MODE == SG_DENSE_T) {
+    x = o.p[(int64_t)(o.c0 + col) + (int64_t)(o.r0 + row) * o.ld];
+  } else if constexpr (MODE == SG_QHAT || MODE == SG_QHAT_T) {
+    const int j = MODE == SG_QHAT ? o.r0 + row : o.c0 + col;    // Qhat(j, i)
+    const int i = MODE == SG_QHAT ? o.c0 + col : o.r0 + row;
+    x = o.wcol[i][j] * o.sinv[i];
+    if (o.lid) ok = ok && o.lid[i] != o.lid[j];
+  } else if constexpr (MODE == SG_XCOLS) {
+    const int j = o.c0 + col;
+    x = o.xcol[j][row];
+    ok = ok && row >= o.xlo[j] && row < o.xhi[j];
+  } else if constexpr (MODE == SG_STACK) {
+    const bool first = col < o.k1;
+    x = first ? o.p[(int64_t)(o.r0 + row) + (int64_t)col * o.ld]
+              : o.p2[(int64_t)(o.r0 + row) + (int64_t)(col - o.k1) * o.ld2];
+  } else {
+    const bool first = row < o.k1;
+    x = first ? o.p[(int64_t)row + (int64_t)(o.c0 + col) * o.ld]
+              : o.p2[(int64_t)(row - o.k1) + (int64_t)(o.c0 + col) * o.ld2];
+  }
+  return ok ? x : 0.0;
+}
 
 // rows of A, 32 per block: the row's power of two, then its digits, 64 k at a time
 // through shared memory; lanes run along whichever index is contiguous in memory
-template <int S>
+template <int S, int MODE>
 __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jobs, int njobs,
                                                     const int64_t* __restrict__ cum) {
   __shared__ double tile[64][33];
@@ -904,34 +915,46 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   const int M = J.M, K = sg_size(J.Kdev, J.K), Me = sg_size(J.Mdev, J.M);
   const SgOp A = sg_resolve(J.a);
   auto at = [&](int r, int k) -> double {          // A[r0 + r, k], zero outside
-    if (r0 + r >= Me || k >= K) return 0.0;
-    return sg_at(A, r0 + r, k);
+    return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < K);
   };
-  const bool rowc = sg_rows_contiguous(J.a.mode);
-  // pass 1: row maxima on the magnitude bits
+  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T;   // consecutive rows adjacent in memory
+  // pass 1: row maxima on the magnitude bits, eight independent loads in flight per thread
+  auto mag = [](double x) { return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull; };
   unsigned long long mx = 0ull;
-  if (rowc) {
+  if constexpr (rowc) {                             // lanes along rows, 8 consecutive k per warp
     const int r = tid & 31, kq = tid >> 5;
-    for (int k = kq; k < K; k += 8) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(at(r, k)) & 0x7FFFFFFFFFFFFFFFull;
-      mx = v > mx ? v : mx;
+    for (int k0 = kq * 8; k0 < K; k0 += 64) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) v[kk] = mag(at(r, k0 + kk));
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) mx = v[kk] > mx ? v[kk] : mx;
     }
     s_max[kq][r] = mx;
   } else {                                          // a warp per group of four rows, lanes along k
     const int lane = tid & 31, wq = tid >> 5;
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = wq * 4 + rr;
-      unsigned long long m = 0ull;
-      for (int k = lane; k < K; k += 32) {
-        const unsigned long long v = (unsigned long long)__double_as_longlong(at(r, k)) & 0x7FFFFFFFFFFFFFFFull;
-        m = v > m ? v : m;
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int k = lane; k < K; k += 64) {
+      unsigned long long v[4][2];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        v[rr][0] = mag(at(wq * 4 + rr, k));
+        v[rr][1] = mag(at(wq * 4 + rr, k + 32));
       }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
-        m = o > m ? o : m;
+      for (int rr = 0; rr < 4; ++rr) {
+        m[rr] = v[rr][0] > m[rr] ? v[rr][0] : m[rr];
+        m[rr] = v[rr][1] > m[rr] ? v[rr][1] : m[rr];
       }
-      if (lane == 0) s_max[0][r] = m;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m[rr], off);
+        m[rr] = o > m[rr] ? o : m[rr];
+      }
+      if (lane == 0) s_max[0][wq * 4 + rr] = m[rr];
     }
     if (tid < 32)
       for (int q = 1; q < 8; ++q) s_max[q][tid] = 0ull;
@@ -951,7 +974,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   const int wr = tid >> 3, wk = (tid & 7) * 8;
   const int shift = 8 * S - 1 - s_exp[wr];
   for (int k0 = 0; k0 < J.Kp; k0 += 64) {
-    if (rowc) {
+    if constexpr (rowc) {
       const int r = tid & 31, kq = tid >> 5;
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) tile[kq * 8 + kk][r] = at(r, k0 + kq * 8 + kk);
@@ -988,7 +1011,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
 
 // columns of B, a warp per column (8 per block): the column's power of two, then its
 // digits, each lane 8 consecutive k
-template <int S>
+template <int S, int MODE>
 __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jobs, int njobs,
                                                     const int64_t* __restrict__ cum) {
   const int jb = find_job(cum, njobs, blockIdx.x);
@@ -999,11 +1022,14 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
   const bool live = !J.Ndev || c < *J.Ndev;         // columns past the actual count are zero
   const int K = sg_size(J.Kdev, J.K);
   const SgOp B = sg_resolve(J.b);
-  auto at = [&](int k) -> double { return live && k < K ? sg_at(B, k, c) : 0.0; };
+  auto at = [&](int k) -> double { return sg_ld<MODE>(B, k, c, live && k < K); };
   unsigned long long m = 0ull;
-  for (int k = lane; k < K; k += 32) {
-    const unsigned long long v = (unsigned long long)__double_as_longlong(at(k)) & 0x7FFFFFFFFFFFFFFFull;
-    m = v > m ? v : m;
+  for (int k0 = lane; k0 < K; k0 += 128) {          // four independent loads in flight
+    unsigned long long v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (unsigned long long)__double_as_longlong(at(k0 + 32 * u)) & 0x7FFFFFFFFFFFFFFFull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = v[u] > m ? v[u] : m;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -1351,7 +1377,7 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
 
 size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
   const int S = slices < 5 ? 5 : (slices > 7 ? 7 : slices);
-  size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 3 * rup(((int64_t)pr.size() + 1) * 8, 256);
+  size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 15 * rup(((int64_t)pr.size() + 1) * 8, 256);
   for (const SgProblem& p : pr) {
     const int64_t Kp = rup(p.K, 64);
     b += rup((int64_t)S * p.M * Kp * 2, 256) + rup((int64_t)S * p.N * Kp * 2, 256) + rup((int64_t)p.M * 4, 256) +
@@ -1361,6 +1387,32 @@ size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
 }
 
 namespace {
+constexpr int kSgForms = 7;
+template <int S>
+void launch_slice_a(int form, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
+  switch (form) {
+    case SG_DENSE: k_sg_slice_a<S, SG_DENSE><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_DENSE_T: k_sg_slice_a<S, SG_DENSE_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT: k_sg_slice_a<S, SG_QHAT><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_T: k_sg_slice_a<S, SG_QHAT_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_XCOLS: k_sg_slice_a<S, SG_XCOLS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_STACK: k_sg_slice_a<S, SG_STACK><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    default: k_sg_slice_a<S, SG_STACK_ROWS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+  }
+}
+template <int S>
+void launch_slice_b(int form, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
+  switch (form) {
+    case SG_DENSE: k_sg_slice_b<S, SG_DENSE><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_DENSE_T: k_sg_slice_b<S, SG_DENSE_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT: k_sg_slice_b<S, SG_QHAT><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_T: k_sg_slice_b<S, SG_QHAT_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_XCOLS: k_sg_slice_b<S, SG_XCOLS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_STACK: k_sg_slice_b<S, SG_STACK><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    default: k_sg_slice_b<S, SG_STACK_ROWS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+  }
+}
+
 template <int S>
 int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_bytes, int* err, cudaStream_t st) {
   using C = OzCfg<S>;
@@ -1393,11 +1445,11 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
     return p;
   };
   SgJob* djobs = reinterpret_cast<SgJob*>(take(nj * sizeof(SgJob)));
-  int64_t* dca = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
-  int64_t* dcb = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
+  int64_t* dca = reinterpret_cast<int64_t*>(take(kSgForms * (nj + 1) * 8));   // per form of A
+  int64_t* dcb = reinterpret_cast<int64_t*>(take(kSgForms * (nj + 1) * 8));   // per form of B
   int64_t* dct = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
   std::vector<SgJob> jobs(nj);
-  std::vector<int64_t> ca(nj + 1, 0), cb(nj + 1, 0), ct(nj + 1, 0);
+  std::vector<int64_t> ca(kSgForms * (nj + 1), 0), cb(kSgForms * (nj + 1), 0), ct(nj + 1, 0);
   for (size_t j = 0; j < nj; ++j) {
     const SgProblem& p = pr[j];
     SgJob& J = jobs[j];
@@ -1417,22 +1469,39 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
     J.Kdev = p.Kdev;
     J.alpha = p.alpha;
     J.beta = p.beta;
-    J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
+    const bool shared = p.a_from >= 0 && (size_t)p.a_from < j;
+    if (shared) {
+      const SgJob& src = jobs[p.a_from];
+      if (src.M != J.M || src.Kp != J.Kp) return -1;
+      J.as = src.as;
+      J.aexp = src.aexp;
+      J.mapA = src.mapA;
+    } else {
+      J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
+      J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));
+      if (!encode4d(&J.mapA, J.as, J.Kp, p.M, S, kOzBM)) return 4;
+    }
     J.bs = reinterpret_cast<uint16_t*>(take((size_t)S * p.N * J.Kp * 2));
-    J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));
     J.bexp = reinterpret_cast<int32_t*>(take((size_t)p.N * 4));
-    if (!encode4d(&J.mapA, J.as, J.Kp, p.M, S, kOzBM) || !encode4d(&J.mapB, J.bs, J.Kp, p.N, S, kOzBN)) return 4;
-    ca[j + 1] = ca[j] + (p.M + 31) / 32;
-    cb[j + 1] = cb[j] + (p.N + 7) / 8;
+    if (!encode4d(&J.mapB, J.bs, J.Kp, p.N, S, kOzBN)) return 4;
+    if (p.a.mode < 0 || p.a.mode >= kSgForms || p.b.mode < 0 || p.b.mode >= kSgForms) return -1;
+    for (int f = 0; f < kSgForms; ++f) {
+      const size_t o = (size_t)f * (nj + 1);
+      ca[o + j + 1] = ca[o + j] + (f == p.a.mode && !shared ? (p.M + 31) / 32 : 0);
+      cb[o + j + 1] = cb[o + j] + (f == p.b.mode ? (p.N + 7) / 8 : 0);
+    }
     ct[j + 1] = ct[j] + (int64_t)((p.M + kOzBM - 1) / kOzBM) * ((p.N + kOzBN - 1) / kOzBN);
   }
   if (off > ws_bytes) return 3;
   cudaMemcpyAsync(djobs, jobs.data(), nj * sizeof(SgJob), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(dca, ca.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(dcb, cb.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dca, ca.data(), ca.size() * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dcb, cb.data(), cb.size() * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dct, ct.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
-  if (ca[nj]) k_sg_slice_a<S><<<(unsigned)ca[nj], 256, 0, st>>>(djobs, (int)nj, dca);
-  if (cb[nj]) k_sg_slice_b<S><<<(unsigned)cb[nj], 256, 0, st>>>(djobs, (int)nj, dcb);
+  for (int f = 0; f < kSgForms; ++f) {          // one slicing launch per form present
+    const size_t o = (size_t)f * (nj + 1);
+    if (ca[o + nj]) launch_slice_a<S>(f, (unsigned)ca[o + nj], djobs, (int)nj, dca + o, st);
+    if (cb[o + nj]) launch_slice_b<S>(f, (unsigned)cb[o + nj], djobs, (int)nj, dcb + o, st);
+  }
   if (ct[nj]) {
     const unsigned grid = (unsigned)(ct[nj] < nsm ? ct[nj] : nsm);
     k_sg_gemm<S><<<grid, kThreads, C::SMEM, st>>>(djobs, (int)nj, dct, err);

@@ -74,7 +74,8 @@ int oz_slice_pairs(int slices);
 // C = alpha A B + beta C, column-major with ldc, or through column pointers
 // cptrs[cc0 + col][row].  Mdev, Ndev and Kdev (optional, device) hold the actual sizes
 // (<= M, N, K): A's and B's entries past them count as zero, and C's rows and columns past
-// them are not written.  One call runs a batch: slicing of every A and B, then one
+// them are not written.  A problem may name an earlier one of its batch with the same A
+// (a_from), whose slices it then reads.  One call runs a batch: slicing of every A and B, then one
 // persistent GEMM over all their tiles.  The workspace holds the slices (about
 // 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives its size.
 // Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
@@ -108,6 +109,7 @@ struct SgProblem {
   const int* Ndev = nullptr;
   const int* Kdev = nullptr;
   double alpha = 1.0, beta = 0.0;
+  int a_from = -1;            // an earlier problem of the batch with the same A (M, K, Mdev, Kdev): its slices are reused
 };
 inline SgOp sg_dense(const double* p, int64_t ld, bool trans = false) {
   SgOp o;
