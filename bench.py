@@ -227,6 +227,8 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
         out["split_operand_split_ms"] = p.ms[9]
         out["split_gemm_bf16_tflops"] = p.split_tensor_flops / (p.ms[8] * 1e-3) / 1e12
     out["phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES)}
+    if p.sg_gemm_ms > 0:             # the dense split GEMM kernel (HSS products): bf16 slice-pair rate
+        out["sg_gemm"] = {"ms": p.sg_gemm_ms, "bf16_tflops": p.sg_tensor_flops / (p.sg_gemm_ms * 1e-3) / 1e12}
     if p.ms[10] > 0:                 # HSS: the sampling's FP64-equivalent rate (4 K^2 (r + p) flops, split GEMM)
         out["hss"] = {"sampling_flops": p.hss_sampling_flops,
                       "sampling_fp64_equivalent_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
@@ -261,6 +263,10 @@ def context_measurements(api, _lib, lib, torch):
                                                  exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
     ctx["toeplitz_32768_split_7slices"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki", ozaki_slices=7,
                                                          exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
+    ctx["toeplitz_32768_hss"] = profiled_solve(api, _lib, lib, torch, d, e, "hss",
+                                               exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
+    ctx["toeplitz_32768_auto"] = profiled_solve(api, _lib, lib, torch, d, e, "auto",
+                                                exact=2.0 - 2.0 * np.cos(k * np.pi / 32769))
     d, e = W.uniform_tridiag(32768, 0)
     ctx["uniform_32768_split"] = profiled_solve(api, _lib, lib, torch, d, e, "ozaki")
     d, e = W.graded_tridiag(32768, 0)

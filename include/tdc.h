@@ -319,6 +319,10 @@ typedef struct tdc_profile {
                                                         product (tile count + GEMM)        */
   int64_t secular_evals;           /* FP64 secular-function evaluations, summed over the
                                       roots (the FP32 evaluations are not counted)        */
+  double sg_gemm_ms;               /* event time of the dense split GEMM kernel's launches
+                                      (the HSS products; the backward's split products)   */
+  double sg_tensor_flops;          /* their bf16 tensor flops: slice pairs x 2 M N K per
+                                      product, M, N, K the launch-time sizes               */
 } tdc_profile;
 void tdc_profile_begin(void);
 int tdc_profile_end(tdc_profile* out);

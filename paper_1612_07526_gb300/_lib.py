@@ -57,6 +57,8 @@ class TdcProfile(ctypes.Structure):
         ("level_fp64_flops", ctypes.c_double * 32),
         ("level_fp64_product_ms", ctypes.c_double * 32),
         ("secular_evals", ctypes.c_int64),
+        ("sg_gemm_ms", ctypes.c_double),
+        ("sg_tensor_flops", ctypes.c_double),
     ]
 
 

@@ -489,7 +489,8 @@ struct ProfState {
   double secular_flops = 0.0;
   int64_t secular_evals = 0;
   int64_t merges = 0, ktot = 0, calls = 0, hss_fallbacks = 0, hss_regrowths = 0;
-  double hss_sampling_flops = 0.0;
+  double hss_sampling_flops = 0.0, sg_tensor_flops = 0.0;
+  cudaEvent_t sg_open = nullptr;
   double lvl_bytes[TDC_PROFILE_LEVELS] = {}, lvl_flops[TDC_PROFILE_LEVELS] = {};
   MergeScalars* hscal = nullptr;
   size_t hscal_n = 0;
@@ -537,6 +538,21 @@ void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st) {
     g_prof.recs.push_back(ProfRec{phase, g_prof.open_ev[slot], b});
     g_prof.open_ev[slot] = nullptr;
     if (phase < TDC_NPHASE) g_prof.launches[phase] += nlaunch;
+  }
+}
+
+constexpr int kSgMark = 200;   // ProfRec id of the split GEMM kernel's launches
+void sg_gemm_mark(bool begin, double tensor_flops, cudaStream_t st) {
+  if (!g_prof.on || t_prof_suspended) return;
+  if (begin) {
+    g_prof.sg_open = prof_event();
+    cudaEventRecord(g_prof.sg_open, st);
+    g_prof.sg_tensor_flops += tensor_flops;
+  } else if (g_prof.sg_open) {
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, st);
+    g_prof.recs.push_back(ProfRec{kSgMark, g_prof.sg_open, b});
+    g_prof.sg_open = nullptr;
   }
 }
 
@@ -1015,7 +1031,8 @@ void tdc_profile_begin(void) {
   g_prof.copy_bytes = g_prof.secular_flops = 0.0;
   g_prof.secular_evals = 0;
   g_prof.merges = g_prof.ktot = g_prof.calls = g_prof.hss_fallbacks = g_prof.hss_regrowths = 0;
-  g_prof.hss_sampling_flops = 0.0;
+  g_prof.hss_sampling_flops = g_prof.sg_tensor_flops = 0.0;
+  g_prof.sg_open = nullptr;
   for (int i = 0; i < TDC_NPHASE + TDC_PROFILE_LEVELS; ++i) g_prof.open_ev[i] = nullptr;
   for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) g_prof.lvl_bytes[l] = g_prof.lvl_flops[l] = 0.0;
 }
@@ -1027,7 +1044,8 @@ int tdc_profile_end(tdc_profile* out) {
   for (const ProfRec& r : g_prof.recs) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.a, r.b);
-    if (r.ph >= kLevelMark) out->level_fp64_product_ms[r.ph - kLevelMark] += ms;
+    if (r.ph == kSgMark) out->sg_gemm_ms += ms;
+    else if (r.ph >= kLevelMark) out->level_fp64_product_ms[r.ph - kLevelMark] += ms;
     else out->ms[r.ph] += ms;
   }
   for (int i = 0; i < TDC_NPHASE; ++i) out->launches[i] = g_prof.launches[i];
@@ -1045,6 +1063,7 @@ int tdc_profile_end(tdc_profile* out) {
   out->hss_fallbacks = g_prof.hss_fallbacks;
   out->hss_regrowths = g_prof.hss_regrowths;
   out->hss_sampling_flops = g_prof.hss_sampling_flops;
+  out->sg_tensor_flops = g_prof.sg_tensor_flops;
   for (int l = 0; l < TDC_PROFILE_LEVELS; ++l) {
     out->level_fp64_min_bytes[l] = g_prof.lvl_bytes[l];
     out->level_fp64_flops[l] = g_prof.lvl_flops[l];

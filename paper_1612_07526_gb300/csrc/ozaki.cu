@@ -852,6 +852,7 @@ struct SgJob {                       // CUtensorMap members force 64-byte alignm
   double alpha, beta;
   uint16_t *as, *bs;
   int32_t *aexp, *bexp;              // INT32_MIN: a zero row / column
+  unsigned long long *amax, *bmax;   // row / column maxima of |A|, |B| (magnitude bits)
   int64_t ldc;
   int32_t M, N, K, Kp;               // Kp: K rounded up to 64
   int32_t cc0, pad_;
@@ -900,46 +901,71 @@ __device__ __forceinline__ double sg_ld(const SgOp& o, int row, int col, bool ok
   return ok ? x : 0.0;
 }
 
-// rows of A, 32 per block: the row's power of two, then its digits, 64 k at a time
-// through shared memory; lanes run along whichever index is contiguous in memory
-template <int S, int MODE>
-__global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jobs, int njobs,
-                                                    const int64_t* __restrict__ cum) {
-  __shared__ double tile[64][33];
+// Slicing of the operands, in two launches each so that every block has a bounded
+// share of k and the grid covers the device whatever the operand's shape:
+//   k_sg_amax / k_sg_bmax  partial row (column) maxima of |A| (|B|) over one chunk of k,
+//                          combined with atomicMax on the magnitude bits (integer order =
+//                          order of |x|) into amax / bmax, zeroed before;
+//   k_sg_slice_a / _b      the row's (column's) power of two from that maximum, then the
+//                          digits of the chunk.
+// A: blocks of 32 rows x kSgChunkA k; lanes run along whichever index is contiguous in
+// memory, through shared memory.  B: blocks of 8 columns (a warp each) x kSgChunkB k.
+constexpr int kSgChunkA = 512;
+constexpr int kSgChunkB = 2048;
+__device__ __forceinline__ unsigned long long sg_mag(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int sg_exp_of(unsigned long long mb) {   // 2^(e-1) <= m < 2^e
+  int e = 0;
+  const double m = __longlong_as_double((long long)mb);
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+struct SgABlock {
+  int jb, r0, k0;
+};
+__device__ __forceinline__ SgABlock sg_ablock(const SgJob* __restrict__ jobs, const int64_t* __restrict__ cum,
+                                              int njobs) {
+  SgABlock b;
+  b.jb = find_job(cum, njobs, blockIdx.x);
+  const int64_t local = blockIdx.x - cum[b.jb];
+  const int nkc = (jobs[b.jb].Kp + kSgChunkA - 1) / kSgChunkA;
+  b.r0 = (int)(local / nkc) * 32;
+  b.k0 = (int)(local % nkc) * kSgChunkA;
+  return b;
+}
+
+template <int MODE>
+__global__ __launch_bounds__(256) void k_sg_amax(const SgJob* __restrict__ jobs, int njobs,
+                                                 const int64_t* __restrict__ cum) {
   __shared__ unsigned long long s_max[8][32];
-  __shared__ int s_exp[32];
-  const int jb = find_job(cum, njobs, blockIdx.x);
-  const SgJob& J = jobs[jb];
-  const int r0 = (int)(blockIdx.x - cum[jb]) * 32;
-  const int tid = threadIdx.x;
-  const int M = J.M, K = sg_size(J.Kdev, J.K), Me = sg_size(J.Mdev, J.M);
+  const SgABlock blk = sg_ablock(jobs, cum, njobs);
+  const SgJob& J = jobs[blk.jb];
+  const int r0 = blk.r0, tid = threadIdx.x;
+  const int Me = sg_size(J.Mdev, J.M), kend = min(sg_size(J.Kdev, J.K), blk.k0 + kSgChunkA);
   const SgOp A = sg_resolve(J.a);
-  auto at = [&](int r, int k) -> double {          // A[r0 + r, k], zero outside
-    return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < K);
-  };
+  auto at = [&](int r, int k) -> double { return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < kend); };
   constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T;   // consecutive rows adjacent in memory
-  // pass 1: row maxima on the magnitude bits, eight independent loads in flight per thread
-  auto mag = [](double x) { return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull; };
-  unsigned long long mx = 0ull;
   if constexpr (rowc) {                             // lanes along rows, 8 consecutive k per warp
     const int r = tid & 31, kq = tid >> 5;
-    for (int k0 = kq * 8; k0 < K; k0 += 64) {
+    unsigned long long mx = 0ull;
+    for (int k0 = blk.k0 + kq * 8; k0 < kend; k0 += 64) {
       unsigned long long v[8];
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) v[kk] = mag(at(r, k0 + kk));
+      for (int kk = 0; kk < 8; ++kk) v[kk] = sg_mag(at(r, k0 + kk));
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) mx = v[kk] > mx ? v[kk] : mx;
     }
     s_max[kq][r] = mx;
-  } else {                                          // a warp per group of four rows, lanes along k
+  } else {                                          // a warp per four rows, lanes along k
     const int lane = tid & 31, wq = tid >> 5;
     unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int k = lane; k < K; k += 64) {
+    for (int k = blk.k0 + lane; k < kend; k += 64) {
       unsigned long long v[4][2];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
-        v[rr][0] = mag(at(wq * 4 + rr, k));
-        v[rr][1] = mag(at(wq * 4 + rr, k + 32));
+        v[rr][0] = sg_mag(at(wq * 4 + rr, k));
+        v[rr][1] = sg_mag(at(wq * 4 + rr, k + 32));
       }
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
@@ -960,20 +986,37 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
       for (int q = 1; q < 8; ++q) s_max[q][tid] = 0ull;
   }
   __syncthreads();
-  if (tid < 32) {
+  if (tid < 32 && r0 + tid < Me) {
     unsigned long long mb = s_max[0][tid];
     for (int q = 1; q < 8; ++q) mb = s_max[q][tid] > mb ? s_max[q][tid] : mb;
-    const double m = __longlong_as_double((long long)mb);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);                      // m < 2^e
+    if (mb) atomicMax(J.amax + r0 + tid, mb);
+  }
+}
+
+template <int S, int MODE>
+__global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jobs, int njobs,
+                                                    const int64_t* __restrict__ cum) {
+  __shared__ double tile[64][33];
+  __shared__ int s_exp[32];
+  const SgABlock blk = sg_ablock(jobs, cum, njobs);
+  const SgJob& J = jobs[blk.jb];
+  const int r0 = blk.r0, tid = threadIdx.x;
+  const int M = J.M, K = sg_size(J.Kdev, J.K), Me = sg_size(J.Mdev, J.M), Kp = J.Kp;
+  uint16_t* const as = J.as;
+  const SgOp A = sg_resolve(J.a);
+  auto at = [&](int r, int k) -> double { return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < K); };
+  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T;
+  if (tid < 32) {
+    const unsigned long long mb = r0 + tid < M ? J.amax[r0 + tid] : 0ull;
+    const int e = sg_exp_of(mb);
     s_exp[tid] = e;
-    if (r0 + tid < M) J.aexp[r0 + tid] = m > 0.0 ? e : INT32_MIN;
+    if (blk.k0 == 0 && r0 + tid < M) J.aexp[r0 + tid] = mb ? e : INT32_MIN;
   }
   __syncthreads();
-  // pass 2: digits
   const int wr = tid >> 3, wk = (tid & 7) * 8;
   const int shift = 8 * S - 1 - s_exp[wr];
-  for (int k0 = 0; k0 < J.Kp; k0 += 64) {
+  const int kstop = min(Kp, blk.k0 + kSgChunkA);
+  for (int k0 = blk.k0; k0 < kstop; k0 += 64) {
     if constexpr (rowc) {
       const int r = tid & 31, kq = tid >> 5;
 #pragma unroll
@@ -1001,7 +1044,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
         v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
         v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
         v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
-        *reinterpret_cast<uint4*>(J.as + (((int64_t)p * (J.Kp / kOzBK) + k / kOzBK) * M + r0 + wr) * kOzBK +
+        *reinterpret_cast<uint4*>(as + (((int64_t)p * (Kp / kOzBK) + k / kOzBK) * M + r0 + wr) * kOzBK +
                                   (k % kOzBK)) = v;
       }
     }
@@ -1009,25 +1052,35 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   }
 }
 
-// columns of B, a warp per column (8 per block): the column's power of two, then its
-// digits, each lane 8 consecutive k
-template <int S, int MODE>
-__global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jobs, int njobs,
-                                                    const int64_t* __restrict__ cum) {
-  const int jb = find_job(cum, njobs, blockIdx.x);
-  const SgJob& J = jobs[jb];
-  const int lane = threadIdx.x & 31;
-  const int c = (int)(blockIdx.x - cum[jb]) * 8 + (int)(threadIdx.x >> 5);
+struct SgBBlock {
+  int jb, c, k0;
+};
+__device__ __forceinline__ SgBBlock sg_bblock(const SgJob* __restrict__ jobs, const int64_t* __restrict__ cum,
+                                              int njobs) {
+  SgBBlock b;
+  b.jb = find_job(cum, njobs, blockIdx.x);
+  const int64_t local = blockIdx.x - cum[b.jb];
+  const int nkc = (jobs[b.jb].Kp + kSgChunkB - 1) / kSgChunkB;
+  b.c = (int)(local / nkc) * 8 + (int)(threadIdx.x >> 5);
+  b.k0 = (int)(local % nkc) * kSgChunkB;
+  return b;
+}
+
+template <int MODE>
+__global__ __launch_bounds__(256) void k_sg_bmax(const SgJob* __restrict__ jobs, int njobs,
+                                                 const int64_t* __restrict__ cum) {
+  const SgBBlock blk = sg_bblock(jobs, cum, njobs);
+  const SgJob& J = jobs[blk.jb];
+  const int lane = threadIdx.x & 31, c = blk.c;
   if (c >= J.N) return;                             // uniform over the warp
   const bool live = !J.Ndev || c < *J.Ndev;         // columns past the actual count are zero
-  const int K = sg_size(J.Kdev, J.K);
+  const int kend = min(sg_size(J.Kdev, J.K), blk.k0 + kSgChunkB);
   const SgOp B = sg_resolve(J.b);
-  auto at = [&](int k) -> double { return sg_ld<MODE>(B, k, c, live && k < K); };
   unsigned long long m = 0ull;
-  for (int k0 = lane; k0 < K; k0 += 128) {          // four independent loads in flight
+  for (int k0 = blk.k0 + lane; k0 < kend; k0 += 128) {   // four independent loads in flight
     unsigned long long v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (unsigned long long)__double_as_longlong(at(k0 + 32 * u)) & 0x7FFFFFFFFFFFFFFFull;
+    for (int u = 0; u < 4; ++u) v[u] = sg_mag(sg_ld<MODE>(B, k0 + 32 * u, c, live && k0 + 32 * u < kend));
 #pragma unroll
     for (int u = 0; u < 4; ++u) m = v[u] > m ? v[u] : m;
   }
@@ -1036,17 +1089,31 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
     m = o > m ? o : m;
   }
-  const double mv = __longlong_as_double((long long)m);
-  int e = 0;
-  if (mv > 0.0) frexp(mv, &e);
-  if (lane == 0) J.bexp[c] = mv > 0.0 ? e : INT32_MIN;
+  if (lane == 0 && m) atomicMax(J.bmax + c, m);
+}
+
+template <int S, int MODE>
+__global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jobs, int njobs,
+                                                    const int64_t* __restrict__ cum) {
+  const SgBBlock blk = sg_bblock(jobs, cum, njobs);
+  const SgJob& J = jobs[blk.jb];
+  const int lane = threadIdx.x & 31, c = blk.c;
+  if (c >= J.N) return;                             // uniform over the warp
+  const bool live = !J.Ndev || c < *J.Ndev;
+  const int K = sg_size(J.Kdev, J.K), Kp = J.Kp, N = J.N;
+  uint16_t* const bs = J.bs;
+  const SgOp B = sg_resolve(J.b);
+  const unsigned long long mb = J.bmax[c];
+  const int e = sg_exp_of(mb);
+  if (lane == 0 && blk.k0 == 0) J.bexp[c] = mb ? e : INT32_MIN;
   const int shift = 8 * S - 1 - e;
-  for (int k0 = lane * 8; k0 < J.Kp; k0 += 256) {
+  const int kstop = min(Kp, blk.k0 + kSgChunkB);
+  for (int k0 = blk.k0 + lane * 8; k0 < kstop; k0 += 256) {
     uint16_t dg[8][S];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       uint16_t t[S];
-      digits_bf16<S>(round_scaled(at(k0 + j), shift), t);
+      digits_bf16<S>(round_scaled(sg_ld<MODE>(B, k0 + j, c, live && k0 + j < K), shift), t);
 #pragma unroll
       for (int p = 0; p < S; ++p) dg[j][p] = t[p];
     }
@@ -1057,7 +1124,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_b(const SgJob* __restrict__ jo
       v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
       v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
       v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
-      *reinterpret_cast<uint4*>(J.bs + (((int64_t)p * (J.Kp / kOzBK) + k0 / kOzBK) * J.N + c) * kOzBK +
+      *reinterpret_cast<uint4*>(bs + (((int64_t)p * (Kp / kOzBK) + k0 / kOzBK) * N + c) * kOzBK +
                                 (k0 % kOzBK)) = v;
     }
   }
@@ -1295,20 +1362,42 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
         }
       }
       if (!ok) break;
+      // the job's fields in registers first (the stores below could otherwise alias the
+      // job table for the compiler and force it to reload them), then the output
+      // addresses, exponents and (with beta) old values eight columns at a time, so that
+      // their loads are in flight together
       const int grow = T.row0 + row;
-      const int ncol = sg_size(J.Ndev, J.N);
-      if (grow < sg_size(J.Mdev, J.M)) {
+      const int ncol = sg_size(J.Ndev, J.N), mrow = sg_size(J.Mdev, J.M);
+      double* const* const cptrs = J.cptrs;
+      double* const Cb = J.C;
+      const int64_t ldc = J.ldc;
+      const int cc0 = J.cc0;
+      const double alpha = J.alpha, beta = J.beta;
+      const int32_t* const bexp = J.bexp;
+      if (grow < mrow) {
         const int ea = J.aexp[grow];
+        const int colb = T.ct * kOzBN + half * 32;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = T.ct * kOzBN + half * 32 + j;
-          if (col < ncol) {
-            const int eb = J.bexp[col];
-            double x = (ea == INT32_MIN || eb == INT32_MIN) ? 0.0 : oz_combine(acc[j], tsum[j], eb - 38 + ea);
-            double* dst = J.cptrs ? J.cptrs[J.cc0 + col] + grow : J.C + (int64_t)grow + (int64_t)col * J.ldc;
-            x *= J.alpha;
-            if (J.beta != 0.0) x = fma(J.beta, *dst, x);
-            *dst = x;
+        for (int g = 0; g < 32; g += 8) {
+          double* dst[8];
+          int eb[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = colb + g + j;
+            const bool in = col < ncol;
+            eb[j] = in ? bexp[col] : INT32_MIN;
+            dst[j] = !in ? nullptr : (cptrs ? cptrs[cc0 + col] + grow : Cb + (int64_t)grow + (int64_t)col * ldc);
+          }
+          double old[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) old[j] = (beta != 0.0 && dst[j]) ? *dst[j] : 0.0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (!dst[j]) continue;
+            double x = (ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0 : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea);
+            x *= alpha;
+            if (beta != 0.0) x = fma(beta, old[j], x);
+            *dst[j] = x;
           }
         }
       }
@@ -1378,16 +1467,35 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
 size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
   const int S = slices < 5 ? 5 : (slices > 7 ? 7 : slices);
   size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 15 * rup(((int64_t)pr.size() + 1) * 8, 256);
+  int64_t nmax = 0;
   for (const SgProblem& p : pr) {
     const int64_t Kp = rup(p.K, 64);
     b += rup((int64_t)S * p.M * Kp * 2, 256) + rup((int64_t)S * p.N * Kp * 2, 256) + rup((int64_t)p.M * 4, 256) +
          rup((int64_t)p.N * 4, 256);
+    nmax += p.M + p.N;
   }
-  return b + 256;
+  return b + rup(nmax * 8, 256) + 512;
 }
 
 namespace {
 constexpr int kSgForms = 7;
+// The maxima launch of a form, then its digits launch (same blocks).
+template <int MODE>
+void launch_max(bool a, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
+  if (a) k_sg_amax<MODE><<<grid, 256, 0, st>>>(jobs, nj, cum);
+  else k_sg_bmax<MODE><<<grid, 256, 0, st>>>(jobs, nj, cum);
+}
+void launch_maxima(bool a, int form, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
+  switch (form) {
+    case SG_DENSE: launch_max<SG_DENSE>(a, grid, jobs, nj, cum, st); break;
+    case SG_DENSE_T: launch_max<SG_DENSE_T>(a, grid, jobs, nj, cum, st); break;
+    case SG_QHAT: launch_max<SG_QHAT>(a, grid, jobs, nj, cum, st); break;
+    case SG_QHAT_T: launch_max<SG_QHAT_T>(a, grid, jobs, nj, cum, st); break;
+    case SG_XCOLS: launch_max<SG_XCOLS>(a, grid, jobs, nj, cum, st); break;
+    case SG_STACK: launch_max<SG_STACK>(a, grid, jobs, nj, cum, st); break;
+    default: launch_max<SG_STACK_ROWS>(a, grid, jobs, nj, cum, st); break;
+  }
+}
 template <int S>
 void launch_slice_a(int form, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
   switch (form) {
@@ -1448,6 +1556,11 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
   int64_t* dca = reinterpret_cast<int64_t*>(take(kSgForms * (nj + 1) * 8));   // per form of A
   int64_t* dcb = reinterpret_cast<int64_t*>(take(kSgForms * (nj + 1) * 8));   // per form of B
   int64_t* dct = reinterpret_cast<int64_t*>(take((nj + 1) * 8));
+  size_t nmax = 0;                               // row and column maxima, one zeroed region
+  for (size_t j = 0; j < nj; ++j)
+    nmax += (pr[j].a_from >= 0 && (size_t)pr[j].a_from < j ? 0 : (size_t)pr[j].M) + (size_t)pr[j].N;
+  unsigned long long* maxima = reinterpret_cast<unsigned long long*>(take(nmax * 8));
+  size_t moff = 0;
   std::vector<SgJob> jobs(nj);
   std::vector<int64_t> ca(kSgForms * (nj + 1), 0), cb(kSgForms * (nj + 1), 0), ct(nj + 1, 0);
   for (size_t j = 0; j < nj; ++j) {
@@ -1475,20 +1588,27 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
       if (src.M != J.M || src.Kp != J.Kp) return -1;
       J.as = src.as;
       J.aexp = src.aexp;
+      J.amax = src.amax;
       J.mapA = src.mapA;
     } else {
       J.as = reinterpret_cast<uint16_t*>(take((size_t)S * p.M * J.Kp * 2));
       J.aexp = reinterpret_cast<int32_t*>(take((size_t)p.M * 4));
+      J.amax = maxima + moff;
+      moff += (size_t)p.M;
       if (!encode4d(&J.mapA, J.as, J.Kp, p.M, S, kOzBM)) return 4;
     }
     J.bs = reinterpret_cast<uint16_t*>(take((size_t)S * p.N * J.Kp * 2));
     J.bexp = reinterpret_cast<int32_t*>(take((size_t)p.N * 4));
+    J.bmax = maxima + moff;
+    moff += (size_t)p.N;
     if (!encode4d(&J.mapB, J.bs, J.Kp, p.N, S, kOzBN)) return 4;
     if (p.a.mode < 0 || p.a.mode >= kSgForms || p.b.mode < 0 || p.b.mode >= kSgForms) return -1;
+    const int64_t na = (int64_t)((p.M + 31) / 32) * ((J.Kp + kSgChunkA - 1) / kSgChunkA);
+    const int64_t nb = (int64_t)((p.N + 7) / 8) * ((J.Kp + kSgChunkB - 1) / kSgChunkB);
     for (int f = 0; f < kSgForms; ++f) {
       const size_t o = (size_t)f * (nj + 1);
-      ca[o + j + 1] = ca[o + j] + (f == p.a.mode && !shared ? (p.M + 31) / 32 : 0);
-      cb[o + j + 1] = cb[o + j] + (f == p.b.mode ? (p.N + 7) / 8 : 0);
+      ca[o + j + 1] = ca[o + j] + (f == p.a.mode && !shared ? na : 0);
+      cb[o + j + 1] = cb[o + j] + (f == p.b.mode ? nb : 0);
     }
     ct[j + 1] = ct[j] + (int64_t)((p.M + kOzBM - 1) / kOzBM) * ((p.N + kOzBN - 1) / kOzBN);
   }
@@ -1497,14 +1617,25 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
   cudaMemcpyAsync(dca, ca.data(), ca.size() * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dcb, cb.data(), cb.size() * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dct, ct.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, st);
-  for (int f = 0; f < kSgForms; ++f) {          // one slicing launch per form present
+  if (nmax) cudaMemsetAsync(maxima, 0, nmax * 8, st);
+  for (int f = 0; f < kSgForms; ++f) {          // maxima, then digits, per form present
     const size_t o = (size_t)f * (nj + 1);
-    if (ca[o + nj]) launch_slice_a<S>(f, (unsigned)ca[o + nj], djobs, (int)nj, dca + o, st);
-    if (cb[o + nj]) launch_slice_b<S>(f, (unsigned)cb[o + nj], djobs, (int)nj, dcb + o, st);
+    if (ca[o + nj]) {
+      launch_maxima(true, f, (unsigned)ca[o + nj], djobs, (int)nj, dca + o, st);
+      launch_slice_a<S>(f, (unsigned)ca[o + nj], djobs, (int)nj, dca + o, st);
+    }
+    if (cb[o + nj]) {
+      launch_maxima(false, f, (unsigned)cb[o + nj], djobs, (int)nj, dcb + o, st);
+      launch_slice_b<S>(f, (unsigned)cb[o + nj], djobs, (int)nj, dcb + o, st);
+    }
   }
   if (ct[nj]) {
     const unsigned grid = (unsigned)(ct[nj] < nsm ? ct[nj] : nsm);
+    double tf = 0.0;
+    for (const SgProblem& p : pr) tf += 2.0 * p.M * (double)p.N * (double)p.K;
+    sg_gemm_mark(true, tf * oz_slice_pairs(S), st);
     k_sg_gemm<S><<<grid, kThreads, C::SMEM, st>>>(djobs, (int)nj, dct, err);
+    sg_gemm_mark(false, 0.0, st);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }

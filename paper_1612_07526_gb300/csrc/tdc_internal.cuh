@@ -199,6 +199,9 @@ __device__ __forceinline__ double warp_prod(double v) {
 void phase_mark(int phase, bool begin, int nlaunch, cudaStream_t st);
 // Phase id of tree level l's FP64 product (kLevelMark + l): timed per level.
 constexpr int kLevelMark = 100;
+// Event marks around one launch of the dense split GEMM kernel (begin carries the
+// launch's bf16 slice-pair flops); summed into tdc_profile's sg_gemm fields.
+void sg_gemm_mark(bool begin, double tensor_flops, cudaStream_t st);
 // Counts HSS merges that fell back to the dense product (while profiling is on).
 void hss_fallbacks_add(int n);
 // Counts HSS compressions repeated with a doubled sample (while profiling is on).
