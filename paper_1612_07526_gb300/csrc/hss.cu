@@ -211,19 +211,21 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
 
 // The same row ID on a cluster of kIdCluster CTAs.  CTA q of the cluster holds the
 // columns [q W, q W + W) of M = Phi^T (rows of Phi) in its shared memory (column c
-// at M + c ldm, rows 0..rp-1), so every step works on shared memory only:
-//   1. each CTA offers its unselected column of largest remaining norm; after a
-//      cluster barrier every CTA picks the same pivot p from the kIdCluster offers
-//      (largest norm, then smallest index);
-//   2. the CTA that holds p forms the Householder vector of M(k:, p) from the exact
-//      norm of that column (which also decides the stop: |R_kk| <= tol |R_00|) and
-//      publishes it in its shared memory; after a second barrier every CTA copies it;
-//   3. every CTA reflects its unselected columns (four threads per column) and
-//      downdates their squared norms by R(k, c)^2, recomputing a norm exactly when
-//      the downdate has cancelled it to 2^-26 of its last exact value or below (the
-//      usual safeguard of pivoted QR with norm downdating).
+// at M + c ldm, rows 0..rp-1), so every step works on shared memory, with one cluster
+// barrier per step:
+//   1. after the barrier every CTA reads the kIdCluster offers (each CTA's unselected
+//      column of largest remaining norm, double-buffered by step parity) and picks the
+//      same pivot p (largest norm, then smallest index);
+//   2. every CTA reads M(k:, p) from the shared memory of the CTA that holds it and forms
+//      the same Householder vector from that column's exact norm (which also decides the
+//      stop: |R_kk| <= tol |R_00|); the holder writes R_kk and the zeros below it into
+//      the column only after the next barrier, when every CTA has read it;
+//   3. every CTA reflects its unselected columns (four threads per column), downdates
+//      their squared norms by R(k, c)^2 (recomputing a norm exactly when the downdate
+//      has cancelled it to 2^-26 of its last exact value or below: the usual safeguard
+//      of pivoted QR with norm downdating), and offers its next pivot.
 // The pivot columns are not moved: R11 = M(0:rank, piv) is written to global scratch
-// (row-major), and after a third barrier each CTA solves R11 T(:, c) = M(0:rank, c)
+// (row-major), and after a further barrier each CTA solves R11 T(:, c) = M(0:rank, c)
 // for its other columns and writes its rows of U.
 constexpr int kIdCluster = 8;
 constexpr int kIdThreads = 256;
@@ -236,8 +238,8 @@ IdClShape id_cl_shape(int rows_max, int rp) {
   IdClShape sh;
   sh.W = ((rows_max + kIdCluster - 1) / kIdCluster + 7) / 8 * 8;
   sh.ldm = (rp + 15) / 16 * 16 + 4;          // 4 mod 16 doubles: a warp's quads spread over the banks
-  sh.smem = (size_t)sh.W * sh.ldm * 8 + (size_t)2 * sh.W * 8 + (size_t)rp * 8 + (size_t)(4 + rp) * 8 +
-            (size_t)rp * 4 + (size_t)sh.W * 4 + 64;
+  sh.smem = (size_t)sh.W * sh.ldm * 8 + (size_t)2 * sh.W * 8 + (size_t)rp * 8 + (size_t)rp * 4 +
+            (size_t)sh.W * 4 + 64;
   return sh;
 }
 
@@ -253,15 +255,15 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
   double* nrm = M + (size_t)W * ldm;          // downdated squared norms of M(k:, c)
   double* nref = nrm + W;                     // the same at their last exact computation
   double* v = nref + W;                       // this step's Householder vector (rows k..rp-1)
-  double* pub = v + rp;                       // published by the pivot's CTA: beta, r0, stop, -, v
-  int* piv = reinterpret_cast<int*>(pub + 4 + rp);
+  int* piv = reinterpret_cast<int*>(v + rp);
   int* stc = piv + rp;                        // per column: -2 absent, -1 active, else its step
   __shared__ double s_wv[kIdThreads / 32];
   __shared__ int s_wi[kIdThreads / 32];
-  __shared__ double s_offer_v;
-  __shared__ int s_offer_i;
+  __shared__ double s_offer_v[2];
+  __shared__ int s_offer_i[2];
   __shared__ int s_p;
-  const int tid = threadIdx.x, NT = kIdThreads;
+  __shared__ double s_beta, s_alpha, s_pn;
+  const int tid = threadIdx.x, NT = kIdThreads, lane = tid & 31;
   const int quad = tid >> 2, ql = tid & 3, NQ = NT / 4;
   const int g0 = crank * W;
 
@@ -282,12 +284,8 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
     }
   }
   __syncthreads();
-
-  const int kmax = min(rp, rows);
-  int rank = kmax;
-  double r0 = 0.0;
-  for (int k = 0; k < kmax; ++k) {
-    // 1. this CTA's offer
+  // this CTA's offer: its active column of largest remaining norm (first on ties)
+  auto offer = [&](int slot) {
     double bv = -1.0;
     int bi = 0x7fffffff;
     for (int c = tid; c < W; c += NT)
@@ -298,66 +296,87 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
       const int oi = __shfl_xor_sync(kFullMask, bi, off);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
-    if ((tid & 31) == 0) { s_wv[tid >> 5] = bv; s_wi[tid >> 5] = bi; }
+    if (lane == 0) { s_wv[tid >> 5] = bv; s_wi[tid >> 5] = bi; }
     __syncthreads();
     if (tid == 0) {
       for (int q = 1; q < NT / 32; ++q)
         if (s_wv[q] > bv || (s_wv[q] == bv && s_wi[q] < bi)) { bv = s_wv[q]; bi = s_wi[q]; }
-      s_offer_v = bv;
-      s_offer_i = bi;
+      s_offer_v[slot] = bv;
+      s_offer_i[slot] = bi;
     }
-    cl.sync();                                // offers published
-    if (tid == 0) {
-      double pv = -1.0;
-      int pi = 0x7fffffff;
-      for (int q = 0; q < kIdCluster; ++q) {
-        const double ov = *cl.map_shared_rank(&s_offer_v, q);
-        const int oi = *cl.map_shared_rank(&s_offer_i, q);
-        if (ov > pv || (ov == pv && oi < pi)) { pv = ov; pi = oi; }
+  };
+  offer(0);
+  cl.sync();                                  // step 0's offers published
+
+  const int kmax = min(rp, rows);
+  int rank = kmax;
+  double r0 = 0.0;
+  int pend = -1;                              // this CTA's previous pivot column, R not yet written
+  double pend_alpha = 0.0;
+  for (int k = 0; k < kmax; ++k) {
+    // 1. the pivot
+    if (tid < 32) {
+      double ov = -1.0;
+      int oi = 0x7fffffff;
+      if (lane < kIdCluster) {
+        ov = *cl.map_shared_rank(&s_offer_v[k & 1], lane);
+        oi = *cl.map_shared_rank(&s_offer_i[k & 1], lane);
       }
-      s_p = pi;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double pv = __shfl_xor_sync(kFullMask, ov, off);
+        const int pi = __shfl_xor_sync(kFullMask, oi, off);
+        if (pv > ov || (pv == ov && pi < oi)) { ov = pv; oi = pi; }
+      }
+      if (lane == 0) s_p = oi;
+    }
+    // the previous pivot's column: R_kk and zeros below (every CTA has read it)
+    if (pend >= 0) {
+      double* col = M + (size_t)pend * ldm;
+      for (int r = k - 1 + tid; r < rp; r += NT) col[r] = r == k - 1 ? pend_alpha : 0.0;
+      pend = -1;
     }
     __syncthreads();
     const int p = s_p;                        // the same in every CTA
     if (p == 0x7fffffff) { rank = k; break; }
     const int owner = p / W;
-    // 2. the pivot's CTA: Householder vector of M(k:, p)
-    if (crank == owner && tid < 32) {
-      const int lane = tid;
-      double* col = M + (size_t)(p - g0) * ldm;
+    // 2. the Householder vector of M(k:, p), read from its holder
+    if (tid < 32) {
+      const double* col = cl.map_shared_rank(M + (size_t)(p - owner * W) * ldm, owner);
       double s = 0.0;
-      for (int r = k + lane; r < rp; r += 32) s = fma(col[r], col[r], s);
+      for (int r = k + lane; r < rp; r += 32) {
+        const double x = col[r];
+        v[r] = x;
+        s = fma(x, x, s);
+      }
       s = warp_sum(s);
       const double pn = sqrt(s);
       const double rr0 = k == 0 ? pn : r0;
-      const bool stop = !(pn > tol * rr0);
-      double beta = 0.0;
-      if (!stop) {
-        const double alpha = col[k] >= 0.0 ? -pn : pn;
-        double vv = 0.0;
-        for (int r = k + lane; r < rp; r += 32) {
-          const double vr = col[r] - (r == k ? alpha : 0.0);
-          pub[4 + r] = vr;
-          vv = fma(vr, vr, vv);
-        }
-        vv = warp_sum(vv);
-        beta = vv > 0.0 ? 2.0 / vv : 0.0;
-        __syncwarp();                         // every lane has read col[k]
-        for (int r = k + lane; r < rp; r += 32) col[r] = r == k ? alpha : 0.0;
-        if (lane == 0) stc[p - g0] = k;
+      __syncwarp();
+      const double alpha = v[k] >= 0.0 ? -pn : pn;
+      double vv = 0.0;
+      __syncwarp();                           // every lane has read v[k]
+      for (int r = k + lane; r < rp; r += 32) {
+        const double vr = v[r] - (r == k ? alpha : 0.0);
+        v[r] = vr;
+        vv = fma(vr, vr, vv);
       }
+      vv = warp_sum(vv);
       if (lane == 0) {
-        pub[0] = beta;
-        pub[1] = rr0;
-        pub[2] = stop ? 1.0 : 0.0;
+        s_beta = !(pn > tol * rr0) ? -1.0 : (vv > 0.0 ? 2.0 / vv : 0.0);   // -1: stop
+        s_alpha = alpha;
+        s_pn = pn;
       }
     }
-    cl.sync();                                // Householder vector published
-    const double* opub = cl.map_shared_rank(pub, owner);
-    const double beta = opub[0];
-    if (k == 0) r0 = opub[1];
-    if (opub[2] != 0.0) { rank = k; break; }
-    for (int r = k + tid; r < rp; r += NT) v[r] = opub[4 + r];
+    __syncthreads();
+    const double beta = s_beta;
+    if (k == 0) r0 = s_pn;
+    if (beta < 0.0) { rank = k; break; }
+    if (owner == crank) {
+      pend = p - g0;
+      pend_alpha = s_alpha;
+      if (tid == 0) stc[pend] = k;
+    }
     if (tid == 0) piv[k] = p;
     __syncthreads();
     // 3. reflect the unselected columns, downdate their norms
@@ -393,7 +412,14 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
       }
     }
     __syncthreads();
+    offer((k + 1) & 1);
+    cl.sync();                                // step k + 1's offers published; step k's reads done
   }
+  if (pend >= 0) {                            // the last pivot's column
+    double* col = M + (size_t)pend * ldm;
+    for (int r = rank - 1 + tid; r < rp; r += NT) col[r] = r == rank - 1 ? pend_alpha : 0.0;
+  }
+  __syncthreads();
   // R11 (rank x rank, row-major) to global scratch: R11(i, j) = M(i, piv[j])
   double* R11 = Jb.scratch;
   for (int e = tid; e < W * rank; e += NT) {
@@ -528,7 +554,6 @@ __global__ void k_hss_skel(const HssNodeDev* __restrict__ nodes, const int* __re
 
 __global__ void k_read_k(const MergeScalars* scal, int64_t mid, int* out) { *out = scal[mid].K; }
 
-int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 

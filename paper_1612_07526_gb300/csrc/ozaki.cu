@@ -212,12 +212,18 @@ __device__ __forceinline__ double i64_to_double_bits(long long v) {
   }
   return __longlong_as_double((long long)(s | ((unsigned long long)(1023 + p) << 52) | (q & 0xFFFFFFFFFFFFFull)));
 }
+// The rare cases (subnormal, infinite or NaN operands or results) through ldexp, out of
+// line: inlined, the compiler if-converts them, and their FP64 instructions then issue
+// for every output although no lane takes them.
+__device__ __noinline__ double f32_ldexp_slow(float f, int e) { return ldexp((double)f, e); }
+__device__ __noinline__ double ldexp_slow(double x, int e) { return ldexp(x, e); }
 // f 2^e exactly as a double, for a normal float f and a result in the normal range
 // (the exponent field rebased, the 23 fraction bits moved up); other f through FP64.
 __device__ __forceinline__ double f32_pow2_to_double(float f, int e) {
   const unsigned b = __float_as_uint(f);
   const int ex = (int)((b >> 23) & 0xFFu);
-  if (ex == 0 || ex == 0xFF) return ldexp((double)f, e);  // zero, subnormal, inf, NaN
+  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)(b >> 31) << 63);   // signed zero
+  if (ex == 0 || ex == 0xFF) return f32_ldexp_slow(f, e);  // subnormal, inf, NaN
   return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
                                           ((unsigned long long)(ex - 127 + 1023 + e) << 52) |
                                           ((unsigned long long)(b & 0x7FFFFFu) << 29)));
@@ -226,10 +232,11 @@ __device__ __forceinline__ double f32_pow2_to_double(float f, int e) {
 // through ldexp.
 __device__ __forceinline__ double scale_pow2(double x, int e) {
   const long long b = __double_as_longlong(x);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return x;       // signed zero
   const int ex = (int)((b >> 52) & 0x7FF);
   const int ne = ex + e;
   if (ex != 0 && ex != 0x7FF && ne >= 1 && ne <= 2046) return __longlong_as_double(b + ((long long)e << 52));
-  return ldexp(x, e);
+  return ldexp_slow(x, e);
 }
 // One output of the product: (acc + tsum 2^-8) 2^e, acc in level-5 units, tsum in
 // level-6 units; one FP64 addition.
@@ -1373,6 +1380,9 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
       const int64_t ldc = J.ldc;
       const int cc0 = J.cc0;
       const double alpha = J.alpha, beta = J.beta;
+      // the update's form, uniform per job: branches around whole groups (an FP64
+      // operation under a per-output predicate would still issue on the 2-lane FP64 pipe)
+      const int emode = (alpha == 1.0 && beta == 0.0) ? 0 : ((alpha == 1.0 && beta == 1.0) ? 1 : 2);
       const int32_t* const bexp = J.bexp;
       if (grow < mrow) {
         const int ea = J.aexp[grow];
@@ -1388,16 +1398,27 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
             eb[j] = in ? bexp[col] : INT32_MIN;
             dst[j] = !in ? nullptr : (cptrs ? cptrs[cc0 + col] + grow : Cb + (int64_t)grow + (int64_t)col * ldc);
           }
-          double old[8];
+          if (emode == 0) {                      // C = A B
 #pragma unroll
-          for (int j = 0; j < 8; ++j) old[j] = (beta != 0.0 && dst[j]) ? *dst[j] : 0.0;
+            for (int j = 0; j < 8; ++j)
+              if (dst[j]) *dst[j] = (ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0 : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea);
+          } else {                               // C = alpha A B + beta C
+            double old[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (!dst[j]) continue;
-            double x = (ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0 : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea);
-            x *= alpha;
-            if (beta != 0.0) x = fma(beta, old[j], x);
-            *dst[j] = x;
+            for (int j = 0; j < 8; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+            if (emode == 1) {                      // C += A B
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (dst[j])
+                  *dst[j] = old[j] + ((ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0
+                                      : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (dst[j])
+                  *dst[j] = fma(alpha, (ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0
+                                       : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea), beta * old[j]);
+            }
           }
         }
       }
