@@ -213,7 +213,7 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
 // columns [q W, q W + W) of M = Phi^T (rows of Phi) in its shared memory (column c
 // at M + c ldm, rows 0..rp-1), so every step works on shared memory, with one cluster
 // barrier per step:
-//   1. after the barrier every CTA reads the kIdCluster offers (each CTA's unselected
+//   1. after the barrier every CTA reads the cluster's offers (each warp's unselected
 //      column of largest remaining norm, double-buffered by step parity) and picks the
 //      same pivot p (largest norm, then smallest index);
 //   2. every CTA reads M(k:, p) from the shared memory of the CTA that holds it and forms
@@ -257,10 +257,8 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
   double* v = nref + W;                       // this step's Householder vector (rows k..rp-1)
   int* piv = reinterpret_cast<int*>(v + rp);
   int* stc = piv + rp;                        // per column: -2 absent, -1 active, else its step
-  __shared__ double s_wv[kIdThreads / 32];
-  __shared__ int s_wi[kIdThreads / 32];
-  __shared__ double s_offer_v[2];
-  __shared__ int s_offer_i[2];
+  __shared__ double s_wv[2][kIdThreads / 32];
+  __shared__ int s_wi[2][kIdThreads / 32];
   __shared__ int s_p;
   __shared__ double s_beta, s_alpha, s_pn;
   const int tid = threadIdx.x, NT = kIdThreads, lane = tid & 31;
@@ -284,7 +282,8 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
     }
   }
   __syncthreads();
-  // this CTA's offer: its active column of largest remaining norm (first on ties)
+  // each warp's offer: its active column of largest remaining norm (first on ties),
+  // double-buffered by step parity; the pivot is the best of the cluster's 8 x 8 offers
   auto offer = [&](int slot) {
     double bv = -1.0;
     int bi = 0x7fffffff;
@@ -296,13 +295,9 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
       const int oi = __shfl_xor_sync(kFullMask, bi, off);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
-    if (lane == 0) { s_wv[tid >> 5] = bv; s_wi[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      for (int q = 1; q < NT / 32; ++q)
-        if (s_wv[q] > bv || (s_wv[q] == bv && s_wi[q] < bi)) { bv = s_wv[q]; bi = s_wi[q]; }
-      s_offer_v[slot] = bv;
-      s_offer_i[slot] = bi;
+    if (lane == 0) {
+      s_wv[slot][tid >> 5] = bv;
+      s_wi[slot][tid >> 5] = bi;
     }
   };
   offer(0);
@@ -314,13 +309,25 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
   int pend = -1;                              // this CTA's previous pivot column, R not yet written
   double pend_alpha = 0.0;
   for (int k = 0; k < kmax; ++k) {
-    // 1. the pivot
+    // the previous pivot's column: R_kk and zeros below (every CTA has read it)
+    if (pend >= 0) {
+      double* col = M + (size_t)pend * ldm;
+      for (int r = k - 1 + tid; r < rp; r += NT) col[r] = r == k - 1 ? pend_alpha : 0.0;
+      pend = -1;
+    }
+    // warp 0: the pivot, then the Householder vector of M(k:, p) read from its holder
     if (tid < 32) {
       double ov = -1.0;
       int oi = 0x7fffffff;
-      if (lane < kIdCluster) {
-        ov = *cl.map_shared_rank(&s_offer_v[k & 1], lane);
-        oi = *cl.map_shared_rank(&s_offer_i[k & 1], lane);
+#pragma unroll
+      for (int h = 0; h < (kIdCluster * (kIdThreads / 32) + 31) / 32; ++h) {
+        const int q = lane + 32 * h;
+        if (q < kIdCluster * (kIdThreads / 32)) {
+          const int cta = q / (kIdThreads / 32), wq = q % (kIdThreads / 32);
+          const double v2 = *cl.map_shared_rank(&s_wv[k & 1][wq], cta);
+          const int i2 = *cl.map_shared_rank(&s_wi[k & 1][wq], cta);
+          if (v2 > ov || (v2 == ov && i2 < oi)) { ov = v2; oi = i2; }
+        }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -328,60 +335,53 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
         const int pi = __shfl_xor_sync(kFullMask, oi, off);
         if (pv > ov || (pv == ov && pi < oi)) { ov = pv; oi = pi; }
       }
-      if (lane == 0) s_p = oi;
-    }
-    // the previous pivot's column: R_kk and zeros below (every CTA has read it)
-    if (pend >= 0) {
-      double* col = M + (size_t)pend * ldm;
-      for (int r = k - 1 + tid; r < rp; r += NT) col[r] = r == k - 1 ? pend_alpha : 0.0;
-      pend = -1;
+      const int p = oi;                        // the same in every lane and every CTA
+      if (lane == 0) s_p = p;
+      if (p != 0x7fffffff) {
+        const int owner = p / W;
+        const double* col = cl.map_shared_rank(M + (size_t)(p - owner * W) * ldm, owner);
+        double s = 0.0;
+        for (int r = k + lane; r < rp; r += 32) {
+          const double x = col[r];
+          v[r] = x;
+          s = fma(x, x, s);
+        }
+        s = warp_sum(s);
+        const double pn = sqrt(s);
+        const double rr0 = k == 0 ? pn : r0;
+        __syncwarp();
+        const double alpha = v[k] >= 0.0 ? -pn : pn;
+        __syncwarp();                         // every lane has read v[k]
+        double vv = 0.0;
+        for (int r = k + lane; r < rp; r += 32) {
+          const double vr = v[r] - (r == k ? alpha : 0.0);
+          v[r] = vr;
+          vv = fma(vr, vr, vv);
+        }
+        vv = warp_sum(vv);
+        if (lane == 0) {
+          s_beta = !(pn > tol * rr0) ? -1.0 : (vv > 0.0 ? 2.0 / vv : 0.0);   // -1: stop
+          s_alpha = alpha;
+          s_pn = pn;
+        }
+      }
     }
     __syncthreads();
-    const int p = s_p;                        // the same in every CTA
+    const int p = s_p;
     if (p == 0x7fffffff) { rank = k; break; }
-    const int owner = p / W;
-    // 2. the Householder vector of M(k:, p), read from its holder
-    if (tid < 32) {
-      const double* col = cl.map_shared_rank(M + (size_t)(p - owner * W) * ldm, owner);
-      double s = 0.0;
-      for (int r = k + lane; r < rp; r += 32) {
-        const double x = col[r];
-        v[r] = x;
-        s = fma(x, x, s);
-      }
-      s = warp_sum(s);
-      const double pn = sqrt(s);
-      const double rr0 = k == 0 ? pn : r0;
-      __syncwarp();
-      const double alpha = v[k] >= 0.0 ? -pn : pn;
-      double vv = 0.0;
-      __syncwarp();                           // every lane has read v[k]
-      for (int r = k + lane; r < rp; r += 32) {
-        const double vr = v[r] - (r == k ? alpha : 0.0);
-        v[r] = vr;
-        vv = fma(vr, vr, vv);
-      }
-      vv = warp_sum(vv);
-      if (lane == 0) {
-        s_beta = !(pn > tol * rr0) ? -1.0 : (vv > 0.0 ? 2.0 / vv : 0.0);   // -1: stop
-        s_alpha = alpha;
-        s_pn = pn;
-      }
-    }
-    __syncthreads();
     const double beta = s_beta;
     if (k == 0) r0 = s_pn;
     if (beta < 0.0) { rank = k; break; }
-    if (owner == crank) {
+    if (p / W == crank) {
       pend = p - g0;
       pend_alpha = s_alpha;
-      if (tid == 0) stc[pend] = k;
+      if (tid == 0) stc[pend] = k;            // read by the offers after the next barrier
     }
     if (tid == 0) piv[k] = p;
-    __syncthreads();
-    // 3. reflect the unselected columns, downdate their norms
+    // reflect the unselected columns (the pivot excluded by index: its mark may be in
+    // flight), downdate their norms
     for (int c = quad; c < W; c += NQ) {
-      const bool act = stc[c] == -1;
+      const bool act = stc[c] == -1 && g0 + c != p;
       double* col = M + (size_t)c * ldm;
       double w = 0.0;
       if (act)
