@@ -228,7 +228,13 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
         out["split_gemm_bf16_tflops"] = p.split_tensor_flops / (p.ms[8] * 1e-3) / 1e12
     out["phases_ms"] = {nm: round(p.ms[i], 3) for i, nm in enumerate(_lib.PHASES)}
     if p.sg_gemm_ms > 0:             # the dense split GEMM kernel (HSS products): bf16 slice-pair rate
-        out["sg_gemm"] = {"ms": p.sg_gemm_ms, "bf16_tflops": p.sg_tensor_flops / (p.sg_gemm_ms * 1e-3) / 1e12}
+        pk, src = peaks()
+        rate = p.sg_tensor_flops / (p.sg_gemm_ms * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        out["sg_gemm"] = {"kernel": "k_sg_gemm (split-precision tcgen05 GEMM, all HSS products)", "ms": p.sg_gemm_ms,
+                          "bf16_tflops": rate, "peak": peak, "frac": rate / peak,
+                          "peak_source": f"{src} bf16 sustained",
+                          "flops_basis": "launch-time sizes (device-held ranks below them count as zeros)"}
     if p.ms[10] > 0:                 # HSS: the sampling's FP64-equivalent rate (4 K^2 (r + p) flops, split GEMM)
         out["hss"] = {"sampling_flops": p.hss_sampling_flops,
                       "sampling_fp64_equivalent_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
