@@ -6,7 +6,7 @@
 // off-diagonal low rank).  The decompositions run in FP64:
 //   k_hss_omega   Gaussian sampling matrices (SplitMix64 + Box-Muller)
 //   k_hss_id_cl   column-pivoted QR of Phi^T (row ID Phi ~= U Phi(I, :)), one
-//                 cluster of 8 CTAs per decomposition with Phi^T held in their
+//                 cluster of 2-16 CTAs per decomposition with Phi^T held in their
 //                 shared memory; k_hss_id, one CTA and global scratch, where it
 //                 does not fit
 //   k_hss_couple  per parent: sibling couplings B (Qhat at the skeletons)
@@ -209,7 +209,8 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
   }
 }
 
-// The same row ID on a cluster of kIdCluster CTAs.  CTA q of the cluster holds the
+// The same row ID on a cluster of CS CTAs (2 to 16, chosen per launch so that all its
+// clusters are resident together).  CTA q of the cluster holds the
 // columns [q W, q W + W) of M = Phi^T (rows of Phi) in its shared memory (column c
 // at M + c ldm, rows 0..rp-1), so every step works on shared memory, with one cluster
 // barrier per step:
@@ -227,29 +228,29 @@ __global__ __launch_bounds__(256) void k_hss_id(const HIdJob* __restrict__ jobs,
 // The pivot columns are not moved: R11 = M(0:rank, piv) is written to global scratch
 // (row-major), and after a further barrier each CTA solves R11 T(:, c) = M(0:rank, c)
 // for its other columns and writes its rows of U.
-constexpr int kIdCluster = 8;
 constexpr int kIdThreads = 256;
 
 struct IdClShape {
   int W, ldm;                 // columns per CTA (a multiple of 8), leading dimension of M
   size_t smem;
 };
-IdClShape id_cl_shape(int rows_max, int rp) {
+IdClShape id_cl_shape(int rows_max, int rp, int cs) {
   IdClShape sh;
-  sh.W = ((rows_max + kIdCluster - 1) / kIdCluster + 7) / 8 * 8;
+  sh.W = ((rows_max + cs - 1) / cs + 7) / 8 * 8;
   sh.ldm = (rp + 15) / 16 * 16 + 4;          // 4 mod 16 doubles: a warp's quads spread over the banks
   sh.smem = (size_t)sh.W * sh.ldm * 8 + (size_t)2 * sh.W * 8 + (size_t)rp * 8 + (size_t)rp * 4 +
             (size_t)sh.W * 4 + 64;
   return sh;
 }
 
-__global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads, 1)
+__global__ void __launch_bounds__(kIdThreads, 1)
     k_hss_id_cl(const HIdJob* __restrict__ jobs, double tol, int rp, int W, int ldm) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) double sm_id[];
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank();
-  const HIdJob Jb = jobs[blockIdx.x / kIdCluster];
+  const int CS = (int)cl.num_blocks();         // the cluster size of this launch
+  const HIdJob Jb = jobs[blockIdx.x / CS];
   const int rows = Jb.rows_dev ? *Jb.rows_dev : Jb.rows;
   double* M = sm_id;                          // W x ldm
   double* nrm = M + (size_t)W * ldm;          // downdated squared norms of M(k:, c)
@@ -320,9 +321,9 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
       double ov = -1.0;
       int oi = 0x7fffffff;
 #pragma unroll
-      for (int h = 0; h < (kIdCluster * (kIdThreads / 32) + 31) / 32; ++h) {
+      for (int h = 0; h < (16 * (kIdThreads / 32) + 31) / 32; ++h) {
         const int q = lane + 32 * h;
-        if (q < kIdCluster * (kIdThreads / 32)) {
+        if (q < CS * (kIdThreads / 32)) {
           const int cta = q / (kIdThreads / 32), wq = q % (kIdThreads / 32);
           const double v2 = *cl.map_shared_rank(&s_wv[k & 1][wq], cta);
           const int i2 = *cl.map_shared_rank(&s_wi[k & 1][wq], cta);
@@ -455,25 +456,70 @@ __global__ void __cluster_dims__(kIdCluster, 1, 1) __launch_bounds__(kIdThreads,
   }
 }
 
-// Whether k_hss_id_cl can run with `smem` bytes of shared memory per CTA: at most
-// kIdClMaxSmem, and at least one cluster resident on the device.
+// The cluster size of one k_hss_id_cl launch of `nids` decompositions: the largest of
+// 16, 8, 4 and 2 whose clusters are all resident at once (one wave), else 8 (or the
+// largest that fits its shared memory); 0 when none does (then k_hss_id runs instead).
+// Its shape goes to *sh.
 constexpr size_t kIdClMaxSmem = 200u << 10;
-bool id_cl_usable(size_t smem) {
-  if (smem > kIdClMaxSmem) return false;
-  if (cudaFuncSetAttribute(k_hss_id_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+int id_cl_max_clusters(int cs, size_t smem) {
+  if (cudaFuncSetAttribute(k_hss_id_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (cs > 8 && cudaFuncSetAttribute(k_hss_id_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kIdCluster);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)cs);
   cfg.blockDim = dim3(kIdThreads);
   cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, (void*)k_hss_id_cl, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return n > 0;
+  return n;
+}
+int id_cl_pick(int nids, int rows_max, int rp, IdClShape* sh) {
+  int fallback = 0;
+  IdClShape fsh{};
+  for (int cs = 16; cs >= 2; cs >>= 1) {
+    const IdClShape s = id_cl_shape(rows_max, rp, cs);
+    if (s.smem > kIdClMaxSmem) continue;
+    const int n = id_cl_max_clusters(cs, s.smem);
+    if (n <= 0) continue;
+    if (nids <= n) {                          // the largest size whose clusters fit in one wave
+      *sh = s;
+      return cs;
+    }
+    if (fallback == 0 || cs == 8) {           // else 8 CTAs (more waves of the same clusters
+      fallback = cs;                          // beat fewer, larger CTAs per decomposition)
+      fsh = s;
+    }
+  }
+  *sh = fsh;
+  return fallback;
+}
+cudaError_t launch_id_cl(const HIdJob* jobs, int nids, int cs, const IdClShape& sh, double tol, int rp,
+                         cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(nids * cs));
+  cfg.blockDim = dim3(kIdThreads);
+  cfg.dynamicSmemBytes = sh.smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_hss_id_cl, jobs, tol, rp, sh.W, sh.ldm);
 }
 
 // ------------------------------------------------------------------ parent steps
@@ -821,8 +867,6 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
     phase_mark(11, true, 0, st);
     // ---- interpolative decompositions, leaves to root
     const size_t id_smem = (size_t)(rmax + rp) * 8 + (size_t)rmax * 4 + 64;
-    const IdClShape ish = id_cl_shape(rmax, rp);
-    const bool id_cl = id_cl_usable(ish.smem);
     int* lp = L.lists;
     for (int lev = maxlev; lev >= 1; --lev) {
       std::vector<int> parents, all;
@@ -865,11 +909,12 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
       HIdJob* did = reinterpret_cast<HIdJob*>(tab + toff);
       cudaMemcpyAsync(did, ids.data(), ids.size() * sizeof(HIdJob), cudaMemcpyHostToDevice, st);
       toff += ids.size() * sizeof(HIdJob);
-      if (id_cl)
-        k_hss_id_cl<<<(unsigned)ids.size() * kIdCluster, kIdThreads, ish.smem, st>>>(did, o.hss_tol, rp, ish.W,
-                                                                                     ish.ldm);
-      else
+      IdClShape ish;
+      const int cs = id_cl_pick((int)ids.size(), rmax, rp, &ish);
+      if (cs == 0 || launch_id_cl(did, (int)ids.size(), cs, ish, o.hss_tol, rp, st) != cudaSuccess) {
+        cudaGetLastError();
         k_hss_id<<<(unsigned)ids.size(), 256, id_smem, st>>>(did, o.hss_tol, rp);
+      }
       cudaMemcpyAsync(lp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st);
       k_hss_skel<<<(unsigned)all.size(), 128, 0, st>>>(L.dnodes, lp);
       lp += all.size();
