@@ -703,7 +703,7 @@ def main():
         # copy-out of one solve overlaps the next solve
         dh = torch.tensor(d).pin_memory()
         eh = torch.tensor(e).pin_memory()
-        steps_p = max(args.steps, 6)
+        steps_p = max(args.steps, 12)
         pipe = api.HostPipeline(n, depth=2, opts=opts)
 
         # the bound: the host link's own device-to-host rate for the same bytes (one
@@ -721,7 +721,17 @@ def main():
                 out.append(8.0 * n * n / (c0.elapsed_time(c1) * 1e-3))
             return out
 
-        for _ in range(2):
+        # untimed warm-up of the host link, then of the pipeline: after tens of seconds
+        # without host transfers (the headline's device-only section before this) the
+        # first copies of a process run at 10-60 GB/s and one of the next few solves
+        # takes several hundred ms; the link is warmed until two copies in a row reach
+        # 90 % of the best seen (at most ten), then eight solves run untimed
+        warm = []
+        for _ in range(10):
+            warm += link_samples(1)
+            if len(warm) >= 2 and min(warm[-2:]) >= 0.9 * max(warm):
+                break
+        for _ in range(8):
             pipe.submit(dh, eh)
         pipe.wait_all()
         link_before = link_samples()
@@ -747,6 +757,7 @@ def main():
         e2e["link_d2h_gbs"] = link / 1e9
         e2e["link_d2h_gbs_before_after"] = [[round(x / 1e9, 1) for x in link_before],
                                             [round(x / 1e9, 1) for x in link_after]]
+        e2e["link_warmup_gbs"] = [round(x / 1e9, 1) for x in warm]
         bound_s = e2e["d2h_bytes_per_step"] / link
         e2e["link_bound_s"] = bound_s
         e2e["frac_of_link_bound"] = bound_s / e2e["value"]
