@@ -851,15 +851,21 @@ int run_hss_merge(const MergeJob& hJ, QBufs qb, DevWs w, unsigned char* arena, s
         if (nd[i].leaf)
           for (int j = tree[i].lo; j < tree[i].hi; ++j) lid[j] = i;
       cudaMemcpyAsync(L.lid, lid.data(), (size_t)K * 4, cudaMemcpyHostToDevice, st);
+      // Qhat = W diag(sinv) (W the unscaled Cauchy columns): Y = W (diag(sinv) Omega1)
+      // and Z = diag(sinv) W^T Omega2, so the K^2 slicing reads W alone and the
+      // 1/||.|| factors go to Omega1's rows and Z's rows (K (r + p) products each)
       SgOp qa;
-      qa.mode = SG_QHAT;
+      qa.mode = SG_QHAT_RAW;
       qa.wcol = q.wcol;
-      qa.sinv = q.sinv;
       qa.lid = nn > 1 ? L.lid : nullptr;
       SgOp qt = qa;
-      qt.mode = SG_QHAT_T;
-      std::vector<SgProblem> g{sg_problem(K, rp, K, qa, sg_dense(L.om1, K), L.Y, K),
+      qt.mode = SG_QHAT_T_RAW;
+      SgOp o1 = sg_dense(L.om1, K);
+      o1.mode = SG_DENSE_RS;
+      o1.rs = q.sinv;
+      std::vector<SgProblem> g{sg_problem(K, rp, K, qa, o1, L.Y, K),
                                sg_problem(K, rp, K, qt, sg_dense(L.om2, K), L.Z, K)};
+      g[1].crow = q.sinv;
       const int rc = split_gemm(g, kHssSlices, split_ws, split_bytes, w.status + hJ.prob, st);
       if (rc) return rc == 3 ? 3 : 4;
     }

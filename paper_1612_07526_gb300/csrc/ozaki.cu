@@ -857,6 +857,7 @@ struct SgJob {                       // CUtensorMap members force 64-byte alignm
   double* const* cptrs;
   const int *Mdev, *Ndev, *Kdev;     // actual sizes (device), or null
   double alpha, beta;
+  const double* crow;                // row scales of C (with alpha = 1, beta = 0), or null
   uint16_t *as, *bs;
   int32_t *aexp, *bexp;              // INT32_MIN: a zero row / column
   unsigned long long *amax, *bmax;   // row / column maxima of |A|, |B| (magnitude bits)
@@ -875,7 +876,7 @@ __device__ __forceinline__ SgOp sg_resolve(const SgOp& o) {
 }
 __device__ __forceinline__ int sg_size(const int* dev, int host) { return dev ? min(*dev, host) : host; }
 // Element (row, col) of an operand in the SG_* form MODE (the forms are listed with
-// SgOp), without branches: an element outside the
+// SgOp), without branches (but for the live-row test of SG_XCOLS): an element outside the
 // operand (ok false) is read at the operand's first element and replaced by zero, so that
 // the loads of several elements can be in flight together.
 template <int MODE>
@@ -887,20 +888,24 @@ __device__ __forceinline__ double sg_ld(const SgOp& o, int row, int col, bool ok
     x = o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld];
   } else if constexpr (MODE == SG_DENSE_T) {
     x = o.p[(int64_t)(o.c0 + col) + (int64_t)(o.r0 + row) * o.ld];
-  } else if constexpr (MODE == SG_QHAT || MODE == SG_QHAT_T) {
-    const int j = MODE == SG_QHAT ? o.r0 + row : o.c0 + col;    // Qhat(j, i)
-    const int i = MODE == SG_QHAT ? o.c0 + col : o.r0 + row;
-    x = o.wcol[i][j] * o.sinv[i];
+  } else if constexpr (MODE == SG_QHAT || MODE == SG_QHAT_T || MODE == SG_QHAT_RAW || MODE == SG_QHAT_T_RAW) {
+    constexpr bool tr = MODE == SG_QHAT_T || MODE == SG_QHAT_T_RAW;
+    const int j = tr ? o.c0 + col : o.r0 + row;                 // Qhat(j, i)
+    const int i = tr ? o.r0 + row : o.c0 + col;
+    if constexpr (MODE == SG_QHAT || MODE == SG_QHAT_T) x = o.wcol[i][j] * o.sinv[i];
+    else x = o.wcol[i][j];
     if (o.lid) ok = ok && o.lid[i] != o.lid[j];
+  } else if constexpr (MODE == SG_DENSE_RS) {
+    x = o.p[(int64_t)(o.r0 + row) + (int64_t)(o.c0 + col) * o.ld] * o.rs[o.r0 + row];
   } else if constexpr (MODE == SG_XCOLS) {
     const int j = o.c0 + col;
-    x = o.xcol[j][row];
     ok = ok && row >= o.xlo[j] && row < o.xhi[j];
+    x = ok ? o.xcol[j][row] : 0.0;             // rows outside the live range are not read
   } else if constexpr (MODE == SG_STACK) {
     const bool first = col < o.k1;
     x = first ? o.p[(int64_t)(o.r0 + row) + (int64_t)col * o.ld]
               : o.p2[(int64_t)(o.r0 + row) + (int64_t)(col - o.k1) * o.ld2];
-  } else {
+  } else {                                  // SG_STACK_ROWS
     const bool first = row < o.k1;
     x = first ? o.p[(int64_t)row + (int64_t)(o.c0 + col) * o.ld]
               : o.p2[(int64_t)(row - o.k1) + (int64_t)(o.c0 + col) * o.ld2];
@@ -952,7 +957,7 @@ __global__ __launch_bounds__(256) void k_sg_amax(const SgJob* __restrict__ jobs,
   const int Me = sg_size(J.Mdev, J.M), kend = min(sg_size(J.Kdev, J.K), blk.k0 + kSgChunkA);
   const SgOp A = sg_resolve(J.a);
   auto at = [&](int r, int k) -> double { return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < kend); };
-  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T;   // consecutive rows adjacent in memory
+  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T && MODE != SG_QHAT_T_RAW;   // consecutive rows adjacent in memory
   if constexpr (rowc) {                             // lanes along rows, 8 consecutive k per warp
     const int r = tid & 31, kq = tid >> 5;
     unsigned long long mx = 0ull;
@@ -1012,7 +1017,7 @@ __global__ __launch_bounds__(256) void k_sg_slice_a(const SgJob* __restrict__ jo
   uint16_t* const as = J.as;
   const SgOp A = sg_resolve(J.a);
   auto at = [&](int r, int k) -> double { return sg_ld<MODE>(A, r0 + r, k, r0 + r < Me && k < K); };
-  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T;
+  constexpr bool rowc = MODE != SG_DENSE_T && MODE != SG_QHAT_T && MODE != SG_QHAT_T_RAW;
   if (tid < 32) {
     const unsigned long long mb = r0 + tid < M ? J.amax[r0 + tid] : 0ull;
     const int e = sg_exp_of(mb);
@@ -1382,7 +1387,8 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
       const double alpha = J.alpha, beta = J.beta;
       // the update's form, uniform per job: branches around whole groups (an FP64
       // operation under a per-output predicate would still issue on the 2-lane FP64 pipe)
-      const int emode = (alpha == 1.0 && beta == 0.0) ? 0 : ((alpha == 1.0 && beta == 1.0) ? 1 : 2);
+      const double* const crow = J.crow;
+      const int emode = crow ? 3 : ((alpha == 1.0 && beta == 0.0) ? 0 : ((alpha == 1.0 && beta == 1.0) ? 1 : 2));
       const int32_t* const bexp = J.bexp;
       if (grow < mrow) {
         const int ea = J.aexp[grow];
@@ -1402,6 +1408,13 @@ __global__ __launch_bounds__(kThreads, 1) void k_sg_gemm(const SgJob* __restrict
 #pragma unroll
             for (int j = 0; j < 8; ++j)
               if (dst[j]) *dst[j] = (ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0 : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea);
+          } else if (emode == 3) {               // C = diag(crow) A B
+            const double cr = crow[grow];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (dst[j])
+                *dst[j] = cr * ((ea == INT32_MIN || eb[j] == INT32_MIN) ? 0.0
+                                : oz_combine(acc[g + j], tsum[g + j], eb[j] - 38 + ea));
           } else {                               // C = alpha A B + beta C
             double old[8];
 #pragma unroll
@@ -1499,7 +1512,7 @@ size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
 }
 
 namespace {
-constexpr int kSgForms = 7;
+constexpr int kSgForms = 10;
 // The maxima launch of a form, then its digits launch (same blocks).
 template <int MODE>
 void launch_max(bool a, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
@@ -1514,6 +1527,9 @@ void launch_maxima(bool a, int form, unsigned grid, const SgJob* jobs, int nj, c
     case SG_QHAT_T: launch_max<SG_QHAT_T>(a, grid, jobs, nj, cum, st); break;
     case SG_XCOLS: launch_max<SG_XCOLS>(a, grid, jobs, nj, cum, st); break;
     case SG_STACK: launch_max<SG_STACK>(a, grid, jobs, nj, cum, st); break;
+    case SG_QHAT_RAW: launch_max<SG_QHAT_RAW>(a, grid, jobs, nj, cum, st); break;
+    case SG_QHAT_T_RAW: launch_max<SG_QHAT_T_RAW>(a, grid, jobs, nj, cum, st); break;
+    case SG_DENSE_RS: launch_max<SG_DENSE_RS>(a, grid, jobs, nj, cum, st); break;
     default: launch_max<SG_STACK_ROWS>(a, grid, jobs, nj, cum, st); break;
   }
 }
@@ -1526,6 +1542,9 @@ void launch_slice_a(int form, unsigned grid, const SgJob* jobs, int nj, const in
     case SG_QHAT_T: k_sg_slice_a<S, SG_QHAT_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     case SG_XCOLS: k_sg_slice_a<S, SG_XCOLS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     case SG_STACK: k_sg_slice_a<S, SG_STACK><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_RAW: k_sg_slice_a<S, SG_QHAT_RAW><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_T_RAW: k_sg_slice_a<S, SG_QHAT_T_RAW><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_DENSE_RS: k_sg_slice_a<S, SG_DENSE_RS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     default: k_sg_slice_a<S, SG_STACK_ROWS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
   }
 }
@@ -1538,6 +1557,9 @@ void launch_slice_b(int form, unsigned grid, const SgJob* jobs, int nj, const in
     case SG_QHAT_T: k_sg_slice_b<S, SG_QHAT_T><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     case SG_XCOLS: k_sg_slice_b<S, SG_XCOLS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     case SG_STACK: k_sg_slice_b<S, SG_STACK><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_RAW: k_sg_slice_b<S, SG_QHAT_RAW><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_QHAT_T_RAW: k_sg_slice_b<S, SG_QHAT_T_RAW><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
+    case SG_DENSE_RS: k_sg_slice_b<S, SG_DENSE_RS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
     default: k_sg_slice_b<S, SG_STACK_ROWS><<<grid, 256, 0, st>>>(jobs, nj, cum); break;
   }
 }
@@ -1603,6 +1625,8 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
     J.Kdev = p.Kdev;
     J.alpha = p.alpha;
     J.beta = p.beta;
+    J.crow = p.crow;
+    if (p.crow && (p.alpha != 1.0 || p.beta != 0.0)) return -1;
     const bool shared = p.a_from >= 0 && (size_t)p.a_from < j;
     if (shared) {
       const SgJob& src = jobs[p.a_from];

@@ -68,10 +68,12 @@ int oz_slice_pairs(int slices);
 //                (gathered eigenvector columns with their nonzero row ranges)
 //   SG_STACK     [P P2]: p[(r0 + row) + col ld] for col < k1, else p2[(r0 + row) + (col - k1) ld2]
 //   SG_STACK_ROWS [P; P2]: p[row + (c0 + col) ld] for row < k1, else p2[(row - k1) + (c0 + col) ld2]
+//   SG_QHAT_RAW, SG_QHAT_T_RAW  SG_QHAT, SG_QHAT_T without the sinv factor (wcol only)
+//   SG_DENSE_RS  SG_DENSE with row (r0 + row) scaled by rs[r0 + row]
 // with k1 = *split (device).  In SG_DENSE_T, off_dev (optional, device) adds to c0.  In
 // the SG_QHAT forms, lid (optional) gives a block index per Qhat index, and entries whose
 // row and column share a block read as zero (Qhat without its diagonal blocks).
-// C = alpha A B + beta C, column-major with ldc, or through column pointers
+// C = alpha A B + beta C (or, with crow, C = diag(crow) A B), column-major with ldc, or through column pointers
 // cptrs[cc0 + col][row].  Mdev, Ndev and Kdev (optional, device) hold the actual sizes
 // (<= M, N, K): A's and B's entries past them count as zero, and C's rows and columns past
 // them are not written.  A problem may name an earlier one of its batch with the same A
@@ -80,7 +82,7 @@ int oz_slice_pairs(int slices);
 // 2 S (M + N) K bytes per problem) and the job table; split_gemm_bytes gives its size.
 // Returns 0, -1 (an empty or null operand), 3 (workspace too small) or 4.
 enum : int { SG_DENSE = 0, SG_DENSE_T = 1, SG_QHAT = 2, SG_QHAT_T = 3, SG_XCOLS = 4, SG_STACK = 5,
-             SG_STACK_ROWS = 6 };
+             SG_STACK_ROWS = 6, SG_QHAT_RAW = 7, SG_QHAT_T_RAW = 8, SG_DENSE_RS = 9 };
 struct SgOp {
   int mode = SG_DENSE;
   int r0 = 0, c0 = 0;
@@ -94,6 +96,7 @@ struct SgOp {
   double* const* wcol = nullptr;
   const double* sinv = nullptr;
   const int32_t* lid = nullptr;
+  const double* rs = nullptr;       // SG_DENSE_RS: row scales
   const double* const* xcol = nullptr;
   const int32_t* xlo = nullptr;
   const int32_t* xhi = nullptr;
@@ -109,6 +112,7 @@ struct SgProblem {
   const int* Ndev = nullptr;
   const int* Kdev = nullptr;
   double alpha = 1.0, beta = 0.0;
+  const double* crow = nullptr;     // optional: C's row r scaled by crow[r] (with alpha = 1, beta = 0)
   int a_from = -1;            // an earlier problem of the batch with the same A (M, K, Mdev, Kdev): its slices are reused
 };
 inline SgOp sg_dense(const double* p, int64_t ld, bool trans = false) {
