@@ -73,7 +73,11 @@ def _fortran(q):
 
 
 @pytest.mark.parametrize("n1,n2,seed,leaf,rp", [(600, 600, 5, 128, 64), (700, 555, 6, 128, 64),
-                                                (1024, 1024, 7, 256, 96)])
+                                                (1024, 1024, 7, 256, 96),
+                                                # 512 samples on up to 1024 rows: the row IDs
+                                                # do not fit a cluster's shared memory and take
+                                                # the one-CTA kernel
+                                                (1100, 1100, 9, 1024, 512)])
 def test_merge_hss(api, n1, n2, seed, leaf, rp):
     D, Q, beta = W.merge_problem(n1, n2, seed)
     n = n1 + n2
