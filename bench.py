@@ -240,6 +240,7 @@ def profiled_solve(api, _lib, lib, torch, d, e, path, exact=None, **kw):
                       "sampling_fp64_equivalent_tflops": p.hss_sampling_flops / (p.ms[10] * 1e-3) / 1e12,
                       "regrowths": int(p.hss_regrowths), "dense_fallbacks": int(p.hss_fallbacks)}
     out["K_total"] = int(p.K_total)
+    out["secular_fp64_evals_per_root"] = p.secular_evals / max(int(p.K_total), 1)
     out["accuracy"] = sampled_accuracy(torch, d, e, lam, q)
     if exact is not None:           # closed-form eigenvalues: max |error| / (n eps ||T||)
         lh = lam.cpu().numpy()
