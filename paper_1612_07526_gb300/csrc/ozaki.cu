@@ -1498,9 +1498,16 @@ void launch_ozaki_level(int part, const MergeJob* jobs, const OzJob* ozj, int nj
   }
 }
 
+namespace {
+constexpr int kSgForms = 10;                    // the SG_* forms: one slicing launch each
+}  // namespace
+
+// The job table, the per-form block counts of A and B and the tile counts (as
+// split_gemm_s takes them), then each problem's slices, exponents and maxima.
 size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
   const int S = slices < 5 ? 5 : (slices > 7 ? 7 : slices);
-  size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 15 * rup(((int64_t)pr.size() + 1) * 8, 256);
+  const int64_t cum = ((int64_t)pr.size() + 1) * 8;
+  size_t b = rup((int64_t)pr.size() * (int64_t)sizeof(SgJob), 256) + 2 * rup(kSgForms * cum, 256) + rup(cum, 256);
   int64_t nmax = 0;
   for (const SgProblem& p : pr) {
     const int64_t Kp = rup(p.K, 64);
@@ -1512,7 +1519,6 @@ size_t split_gemm_bytes(const std::vector<SgProblem>& pr, int slices) {
 }
 
 namespace {
-constexpr int kSgForms = 10;
 // The maxima launch of a form, then its digits launch (same blocks).
 template <int MODE>
 void launch_max(bool a, unsigned grid, const SgJob* jobs, int nj, const int64_t* cum, cudaStream_t st) {
