@@ -1615,7 +1615,7 @@ int split_gemm_s(const std::vector<SgProblem>& pr, unsigned char* ws, size_t ws_
   for (size_t j = 0; j < nj; ++j) {
     const SgProblem& p = pr[j];
     SgJob& J = jobs[j];
-    std::memset(&J, 0, sizeof(J));
+    J = SgJob{};
     J.M = p.M;
     J.N = p.N;
     J.K = p.K;
