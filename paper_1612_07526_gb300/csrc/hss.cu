@@ -729,9 +729,10 @@ void hss_layout(HssLayout& L, unsigned char* base, int K, int m, const tdc_opts&
 // The largest sample an HSS merge may grow to: r + p doubled hss_grow times.
 int hss_rp_max(const tdc_opts& o) { return o.hss_rp << std::max(0, std::min(o.hss_grow, 4)); }
 
-// The split-precision GEMMs of an HSS merge (sampling, and the leaf-level products of
-// the multiply) use 7 slices: the sampled Y feeds rank decisions at the compression
-// tolerance, and 6 slices left noise of about 2e-12 relative in Y at K = 16384.
+// The split-precision GEMMs of an HSS merge (every product of the sampling, the
+// compression and the multiply) use 7 slices: the sampled Y feeds rank decisions at the
+// compression tolerance, and 6 slices left noise of about 2e-12 relative in Y at
+// K = 16384; the multiply's products write the eigenvectors themselves.
 constexpr int kHssSlices = 7;
 
 // Workspace of the split GEMMs of one HSS merge of order m (K <= m kept columns, rp
